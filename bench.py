@@ -1,0 +1,359 @@
+#!/usr/bin/env python
+"""Benchmark: MG-PCG solves/s of tensor-product spline smoothing on one GB300.
+
+One step = sps_set_points (sort, work lists, diagonals, right-hand side,
+coarse matrix, damping) + sps_solve to the workload's tolerance, i.e. the
+whole solve path, with the inputs already resident in HBM.  Default workload:
+P = 3 cubic splines on 64^3 intervals (K = 300,763), n = 1,000,000 clustered
+points (3-component Gaussian mixture clipped to [0,1]^3), lambda = 1e-4,
+6 levels, FP64, |r| <= 1e-8 |Phi'y|.
+
+Launch: `python bench.py [--gpus N --steps K --warmup W]`; for N > 1 under
+torchrun every rank solves its own replica (no collective on the data path)
+and the job value is all solves / max rank time.
+`--impl reference` times the CPU oracle on a bounded sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "MG-PCG solves/s & operator Gpoint-applies/s at rel.res 1e-8; p50/p99 vs plain FP64"
+
+
+def make_problem(name: str, n: int | None):
+    if name == "scale":
+        return W.scale(n=n or 1_000_000)
+    if name == "pr1":
+        return W.pr1(n=n or 2000)
+    if name == "mixed":
+        return W.mixed(n=n or 4_000_000)
+    raise ValueError(name)
+
+
+def workload_desc(pr) -> str:
+    return "%s: P=%d q=3 N=%s (K=%d) n=%d levels=%d lambda=%g tol=%g %s" % (
+        pr.name, pr.P, "x".join(str(v) for v in pr.intervals), pr.K, pr.n, pr.levels, pr.lam, pr.tol,
+        "FP32 x/y, mixed precision" if pr.precision == "mixed" else "FP64")
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- reference arm (CPU oracle)
+
+def oracle_sample(pr, sweeps_per_solve: float, n_sample: int, reps: int) -> dict:
+    """Time the oracle's matrix-free apply u = Phi'(Phi v) on the first
+    n_sample points and scale to solves/s of the full workload:
+    t_solve = sweeps_per_solve * t_sample * n / n_sample.  The oracle's
+    penalty, transfer and setup work is not counted, which favours it."""
+    from oracle import sampled
+    v = np.random.default_rng(0).standard_normal(pr.K)
+    xs = pr.x[:n_sample]
+    best = math.inf
+    t_all = 0.0
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        sampled.apply_phitphi_chunked(xs, v, pr.lo, pr.hi, pr.intervals, pr.q)
+        dt = time.perf_counter() - t0
+        t_all += dt
+        best = min(best, dt)
+    t_sweep = best * pr.n / n_sample
+    t_solve = sweeps_per_solve * t_sweep
+    return {"value": 1.0 / t_solve, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": ("oracle Phi'(Phi v) on %d of %d points, best of %d (%.1f s CPU), scaled by n and by "
+                       "%.0f point sweeps per solve; penalty/transfer/setup not counted" %
+                       (n_sample, pr.n, reps, t_all, sweeps_per_solve)),
+            "sweep_s_full": t_sweep}
+
+
+def sweeps_per_solve(iters: int, levels: int, nu1: int = 1, nu2: int = 1) -> float:
+    # outer apply + per V-cycle (nu1 + nu2 + 1) sweeps on every level above the coarsest,
+    # one V-cycle before the loop and one per iteration
+    return iters + (iters + 1) * (nu1 + nu2 + 1) * (levels - 1)
+
+
+def run_reference(args, pr):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    iters = args.ref_iters
+    sw = sweeps_per_solve(iters, pr.levels)
+    n_sample = min(pr.n, args.ref_sample)
+    for _ in range(args.warmup):
+        oracle_sample(pr, sw, min(n_sample, 20000), 1)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(oracle_sample(pr, sw, n_sample, 1)["value"])
+    wall = time.perf_counter() - t0
+    v = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_desc(pr), "sample_points": n_sample, "sweeps_per_solve": sw},
+            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": "oracle Phi'(Phi v) on %d points per step, scaled to %d points x %.0f sweeps"
+                                       % (n_sample, pr.n, sw)},
+            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": wall}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+
+def run_ours(args, pr):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1901_00654_gb300 import binding as B
+    from paper_1901_00654_gb300 import build as libbuild
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    libbuild.build_library()
+    B.lib()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    mixed = pr.precision == "mixed"
+    xdt = torch.float32 if pr.x.dtype == np.float32 else torch.float64
+    x_d = torch.from_numpy(np.ascontiguousarray(pr.x)).to(dev)
+    y_d = torch.from_numpy(np.ascontiguousarray(pr.y)).to(dev)
+    prec = B.SPS_PREC_MIXED if mixed else B.SPS_PREC_FP64
+    plan = B.Plan(pr.P, pr.intervals, pr.levels, pr.lam, pr.lo, pr.hi, precision=prec)
+    coef = torch.zeros(plan.K, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 129 MB L2
+
+    def step():
+        plan.set_points(x_d, y_d)
+        _, res = plan.solve(pr.tol, coef)
+        return res
+
+    for _ in range(max(args.warmup, 3)):
+        res = step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, L2 flushed before each, CUDA events on the launch stream
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    ids = [v for v in vis.split(",") if v.strip().isdigit()]
+    clocks = ClockSampler(int(ids[local]) if local < len(ids) else local)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = B.sps_launch_count()
+    B.sps_profile_begin()
+    results = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        starts[k].record(stream)
+        results.append(step())
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    point_ms, point_launches = B.sps_profile_end()
+    launches = B.sps_launch_count() - launches0
+    barrier()
+    clk = clocks.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    max_ms = float(t.item())
+    value = world * args.steps / (max_ms * 1e-3)
+    res = results[-1]
+
+    # ---- operator apply throughput on the finest level (FP64 and FP32 kernels)
+    def time_apply(fn, reps=20):
+        v = torch.randn(plan.K, dtype=torch.float64, device=dev)
+        u = torch.zeros_like(v)
+        for _ in range(3):
+            fn(plan.h, pr.levels, v, u)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        total = 0.0
+        for _ in range(reps):
+            flush.fill_(1.0)
+            e0.record(stream)
+            fn(plan.h, pr.levels, v, u)
+            e1.record(stream)
+            e1.synchronize()
+            total += e0.elapsed_time(e1)
+        return total / reps
+
+    apply64 = time_apply(lambda h, g, v, u: B.sps_apply(h, g, B.SPS_PREC_FP64, v, u))
+    point64 = time_apply(lambda h, g, v, u: B.sps_point_apply(h, g, B.SPS_PREC_FP64, v, u))
+
+    # ---- roofline of the dominant kernel (point operator, apply mode), timed inside the steps
+    fma_pt = 2 * 4 ** pr.P                       # gather + scatter multiply-adds per point
+    flops_launch = 2.0 * fma_pt * pr.n
+    avg_ms = point_ms / max(point_launches, 1)
+    fp64_kernel = not mixed
+    fma_rate = B.sps_probe_fma_rate(fp64=fp64_kernel)
+    achieved = flops_launch / (avg_ms * 1e-3) / 1e12
+    peak = 2.0 * fma_rate / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "k_point (apply mode), %s" % ("FP64" if fp64_kernel else "FP32/FP64 mix"),
+                "flops_per_launch": flops_launch, "avg_launch_ms": avg_ms, "launches": point_launches,
+                "peak_source": "measured %s FMA probe (sps_probe_fma_rate) x 2 flops at run-time clocks"
+                               % ("FP64" if fp64_kernel else "FP32")}
+
+    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
+            "config": {"workload": workload_desc(pr), "step": "set_points (device inputs) + solve",
+                       "l2": "flushed (256 MB write) before every timed step", "parallelism": "replicas"},
+            "iterations": res.iterations, "rel_res_true": res.rel_res_true, "fp64_applies": res.fp64_applies,
+            "operator_gpoint_applies_per_s": {"fp64_apply": pr.n / (apply64 * 1e-3) / 1e9,
+                                              "fp64_point_only": pr.n / (point64 * 1e-3) / 1e9},
+            "roofline": roofline, "clocks": clk, "gpu_launches": launches, "step_ms": step_ms}
+
+    if not mixed:
+        point32 = time_apply(lambda h, g, v, u: B.sps_point_apply(h, g, B.SPS_PREC_MIXED, v, u))
+        apply32 = time_apply(lambda h, g, v, u: B.sps_apply(h, g, B.SPS_PREC_MIXED, v, u))
+        line["operator_gpoint_applies_per_s"]["fp32_apply_incl_casts"] = pr.n / (apply32 * 1e-3) / 1e9
+        line["operator_gpoint_applies_per_s"]["fp32_point_incl_casts"] = pr.n / (point32 * 1e-3) / 1e9
+        # the mixed-precision solve of the same workload, beside the plain FP64 one
+        with B.Plan(pr.P, pr.intervals, pr.levels, pr.lam, pr.lo, pr.hi, precision=B.SPS_PREC_MIXED) as pm:
+            cm = torch.zeros(plan.K, dtype=torch.float64, device=dev)
+            for _ in range(2):
+                pm.set_points(x_d, y_d)
+                _, rm = pm.solve(pr.tol, cm)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            tm = 0.0
+            for _ in range(args.steps):
+                flush.fill_(2.0)
+                e0.record(stream)
+                pm.set_points(x_d, y_d)
+                _, rm = pm.solve(pr.tol, cm)
+                e1.record(stream)
+                e1.synchronize()
+                tm += e0.elapsed_time(e1)
+            err = float((cm - coef).abs().max() / coef.abs().max())
+            line["mixed_precision"] = {"solves_per_s": args.steps / (tm * 1e-3), "iterations": rm.iterations,
+                                       "fp64_applies": rm.fp64_applies, "rel_res_true": rm.rel_res_true,
+                                       "coef_rel_err_vs_fp64": err}
+
+    # ---- end to end through the C ABI with pinned host buffers
+    xh = torch.from_numpy(np.ascontiguousarray(pr.x)).pin_memory()
+    yh = torch.from_numpy(np.ascontiguousarray(pr.y)).pin_memory()
+    ch = torch.zeros(plan.K, dtype=torch.float64).pin_memory()
+    xn, yn, cn = xh.numpy(), yh.numpy(), ch.numpy()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        plan.set_points(xn, yn)
+        plan.solve(pr.tol, cn)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    line["e2e"] = {"value": world * args.steps / float(te.item()), "unit": "solves/s",
+                   "h2d_bytes_per_step": int(xn.nbytes + yn.nbytes), "d2h_bytes_per_step": int(cn.nbytes)}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sw = sweeps_per_solve(res.iterations, pr.levels)
+        line["cpu_baseline"] = oracle_sample(pr, sw, min(pr.n, args.ref_sample), 2)
+        line["cpu_baseline"].pop("sweep_s_full", None)
+    plan.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="scale", choices=["scale", "pr1", "mixed"])
+    ap.add_argument("--n", type=int, default=None, help="override the number of points")
+    ap.add_argument("--ref-sample", type=int, default=200_000)
+    ap.add_argument("--ref-iters", type=int, default=12, help="iterations assumed by the reference arm")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    pr = make_problem(args.config, args.n)
+    if args.impl == "reference":
+        run_reference(args, pr)
+    else:
+        run_ours(args, pr)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,211 @@
+/*
+ * sps.h -- C ABI of the GB300 (sm_103a) tensor-product spline smoothing solver.
+ *
+ * The library fits a tensor-product B-spline s(x) = sum_k alpha_k phi_k(x) to
+ * scattered data (x_i, y_i) in R^P x R by solving the penalised normal
+ * equations (Phi'Phi + lambda Lambda) alpha = Phi'y (Siebenborn & Wagner,
+ * arXiv:1901.00654, Section 2.2, the linear system after the smoothing
+ * spline problem) with the multigrid-preconditioned conjugate gradient method
+ * of Algorithm 8, whose preconditioner is the V-cycle of Algorithm 7 with the
+ * damped Jacobi smoother of Algorithm 6.  Every operator is applied matrix
+ * free on the GPU: Phi v and Phi'u by the Khatri-Rao products of Algorithms 3
+ * and 4 (fused into one point operator), Lambda v and the grid transfers by
+ * the Kronecker structure of Algorithm 2.
+ *
+ * Conventions shared by every call:
+ *  - Coefficients are stored row-major over the multi-index (j_1, ..., j_P)
+ *    with the LAST dimension fastest; j_p = 0 .. N_p + q - 1 where N_p is the
+ *    number of knot intervals of dimension p on that grid level.  Basis
+ *    function j_p is the cardinal B-spline on [lo + (j_p - q) h, lo + (j_p + 1) h]
+ *    (extended uniform knots, h = (hi - lo) / N_p).
+ *  - Points are passed as an n x P row-major array (x[i*P + p]).
+ *  - `mem` says where a buffer lives: SPS_MEM_HOST (ordinary or pinned host
+ *    memory) or SPS_MEM_DEVICE (device memory of the plan's GPU).
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *    that return results in host memory synchronise that stream before
+ *    returning; calls with device outputs are asynchronous with respect to the
+ *    host except where stated.
+ *  - Every call returns 0 (SPS_OK) or a negative SPS_E* code; no call aborts
+ *    or throws.  sps_last_error() gives a message for the calling thread's
+ *    most recent failure.
+ *  - Ownership: the caller owns every buffer it passes; the plan owns all of
+ *    its device memory until sps_destroy.  The library copies what it keeps.
+ *  - Level numbers follow the paper: g = 1 is the coarsest grid, g = G (the
+ *    `levels` argument of sps_plan_create) the finest.
+ */
+#ifndef SPS_H
+#define SPS_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SPS_API __attribute__((visibility("default")))
+#else
+#define SPS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define SPS_OK            0
+#define SPS_EINVAL       -1  /* invalid argument (P, q, N_p, levels, lambda, sizes, pointers) */
+#define SPS_EDOM         -2  /* a point lies outside [lo, hi] or is not finite */
+#define SPS_ENOMEM       -3  /* device or host allocation failed */
+#define SPS_ESTATE       -4  /* call out of order (e.g. solve before set_points) */
+#define SPS_EBREAKDOWN   -5  /* CG breakdown: p'Ap <= 0 or a non-finite scalar */
+#define SPS_ENOCONV      -6  /* max_iter reached; coef holds the last iterate */
+#define SPS_ETIMEOUT     -7  /* a device-side loop hit its iteration cap */
+#define SPS_ECUDA        -8  /* a CUDA runtime call failed */
+#define SPS_EEMPTY       -9  /* no data points (n = 0) */
+
+/* ---- enums ---- */
+#define SPS_F32 0            /* float  inputs */
+#define SPS_F64 1            /* double inputs */
+#define SPS_MEM_HOST   0
+#define SPS_MEM_DEVICE 1
+#define SPS_PREC_FP64  0     /* every step in FP64 (plain method) */
+#define SPS_PREC_MIXED 1     /* FP32 V-cycle and FP32 point operator inside an FP64
+                                flexible PCG with FP64 residual replacement */
+
+#define SPS_MAX_DIM    5     /* P <= 5 */
+#define SPS_MAX_LEVELS 12
+
+typedef struct sps_plan sps_plan;       /* opaque; owned by the library */
+
+typedef struct sps_options {
+    int    precision;      /* SPS_PREC_FP64 (default) or SPS_PREC_MIXED */
+    int    nu1, nu2;       /* pre/post Jacobi sweeps per level (default 1, 1) */
+    double omega;          /* Jacobi damping; <= 0 (default): per level
+                              4 / (3 lambda_max(D_g^-1 A_g)) by power iteration */
+    int    power_iters;    /* power iterations for omega (default 20) */
+    int    max_iter;       /* outer iteration cap (default 500) */
+    int    warm_start;     /* 1: coef passed to sps_solve is the initial guess */
+    int    tile;           /* tile side in cells, 0 = automatic per P */
+    double replace_ratio;  /* MIXED: recompute the FP64 residual when |r| has
+                              dropped by this factor since the last recompute
+                              (default 1e-2) */
+} sps_options;
+
+typedef struct sps_result {
+    int    status;         /* SPS_OK, SPS_ENOCONV or SPS_EBREAKDOWN */
+    int    iterations;     /* outer CG iterations (operator applies on level G) */
+    double rel_res;        /* |r| / |Phi'y| of the recursive residual at exit */
+    double rel_res_true;   /* |Phi'y - A alpha| / |Phi'y| recomputed in FP64 at exit */
+    int    fp64_applies;   /* FP64 applies on level G (MIXED: residual replacements) */
+    double solve_ms;       /* wall time of sps_solve (host clock) */
+} sps_result;
+
+/* Fill *opt with the defaults listed above. */
+SPS_API void sps_default_options(sps_options* opt);
+
+/* Create a plan for P-dimensional cubic (q = 3) tensor-product splines.
+ *  intervals[P]: knot intervals N_p of the finest grid, each a power of two,
+ *                N_p >= 2^(levels-1) so the coarsest grid has >= 1 interval.
+ *  lo, hi [P]:   domain Omega = prod [lo_p, hi_p] (NULL -> 0 and 1).
+ *  levels:       number of grid levels G >= 1 (Section 3.2, hierarchy); the
+ *                coarsest has K_1 = prod (N_p / 2^(G-1) + 3) <= 4096 coefficients
+ *                (it is solved densely), and P * log2(max_p N_p) <= 26.
+ *  lambda:       smoothing parameter >= 0 (0 gives the least-squares spline,
+ *                which is SPD only when every basis support holds enough data).
+ *  opt:          NULL for defaults.
+ * Allocates the per-level coefficient vectors on the current CUDA device.
+ * Errors: SPS_EINVAL, SPS_ENOMEM, SPS_ECUDA. */
+SPS_API int sps_plan_create(sps_plan** out, int P, int q, const int* intervals, const double* lo,
+                    const double* hi, int levels, double lambda, const sps_options* opt);
+
+/* Load the data (x_i, y_i), i < n: copies them to the device, validates that
+ * every coordinate is finite and inside [lo_p, hi_p], sorts the points by the
+ * Morton key of their finest knot cell (stable), builds the per-level work
+ * lists, computes diag(A_g) (Algorithm 5 plus the penalty diagonal), the
+ * right-hand side Phi'y (Algorithm 3), the coarse matrix and its inverse, and
+ * omega.  x: n x P row-major, y: n, both of `dtype`, in `mem`.
+ * The caller may free x and y once the call returns.  Synchronises `stream`.
+ * Errors: SPS_EINVAL, SPS_EEMPTY (n == 0), SPS_EDOM, SPS_ENOMEM, SPS_ECUDA. */
+SPS_API int sps_set_points(sps_plan* plan, int64_t n, const void* x, const void* y, int dtype, int mem,
+                   void* stream);
+
+/* Solve (Phi'Phi + lambda Lambda) alpha = Phi'y to |r| <= tol |Phi'y| by
+ * Algorithm 8 (FP64) or its mixed-precision flexible variant.  coef: K_G
+ * doubles in `mem` (input = initial guess when opt.warm_start; output = alpha).
+ * res may be NULL.  Synchronises `stream`.
+ * Errors: SPS_ESTATE (no points), SPS_EINVAL, SPS_ENOCONV, SPS_EBREAKDOWN, SPS_ECUDA. */
+SPS_API int sps_solve(sps_plan* plan, double* coef, int mem, double tol, sps_result* res, void* stream);
+
+/* Release the plan and all of its device memory.  NULL is accepted. */
+SPS_API int sps_destroy(sps_plan* plan);
+
+/* Thread-local message of the last failure (never NULL). */
+SPS_API const char* sps_last_error(void);
+
+/* ---------------- component entry points (each one step of the solve) ----------------
+ * All vectors are doubles in `mem`; `prec` selects the FP64 kernels
+ * (SPS_PREC_FP64) or the FP32 kernels of the mixed mode (SPS_PREC_MIXED, inputs
+ * rounded to FP32 and results widened).  They require sps_set_points and
+ * synchronise `stream` when an output is in host memory. */
+
+/* K_g, the number of coefficients on level g (1 <= g <= G). */
+SPS_API int sps_coef_count(const sps_plan* plan, int level, int64_t* K);
+
+/* u = (Phi_g'Phi_g + lambda Lambda_g) v on level g, with all n points
+ * (Section 3.2, hierarchy; Algorithms 2-4).  v, u: K_g. */
+SPS_API int sps_apply(sps_plan* plan, int level, int prec, const double* v, double* u, int mem, void* stream);
+
+/* u = Phi_g'(Phi_g v) alone: the fused point operator of Algorithms 3 and 4
+ * (no penalty), on level g with all n points.  v, u: K_g. */
+SPS_API int sps_point_apply(sps_plan* plan, int level, int prec, const double* v, double* u, int mem,
+                            void* stream);
+
+/* u = Lambda_g v (penalty alone, Section 2.2; Kronecker sums of Algorithm 2). */
+SPS_API int sps_penalty_apply(sps_plan* plan, int level, int prec, const double* v, double* u, int mem,
+                      void* stream);
+
+/* d = diag(Phi_g'Phi_g + lambda Lambda_g) (Algorithm 5 plus the penalty diagonal). */
+SPS_API int sps_diag(sps_plan* plan, int level, double* d, int mem, void* stream);
+
+/* b = Phi_G'y (Algorithm 3 with the responses). */
+SPS_API int sps_rhs(sps_plan* plan, double* b, int mem, void* stream);
+
+/* f = I_{g-1}^{g} c (prolongation, Section 2.4 subdivision matrix, Kronecker
+ * form); c: K_{g-1}, f: K_g, 2 <= g <= G. */
+SPS_API int sps_prolong(sps_plan* plan, int level, int prec, const double* c, double* f, int mem, void* stream);
+
+/* c = (I_{g-1}^{g})' f (restriction, Section 3.2 grid transfer); f: K_g, c: K_{g-1}. */
+SPS_API int sps_restrict(sps_plan* plan, int level, int prec, const double* f, double* c, int mem, void* stream);
+
+/* e = A_1^{-1} r on the coarsest level (Section 3.2, coarse grid solver). */
+SPS_API int sps_coarse_solve(sps_plan* plan, const double* r, double* e, int mem, void* stream);
+
+/* z = one V-cycle (Algorithm 7) from zero applied to r on level G. */
+SPS_API int sps_vcycle(sps_plan* plan, int prec, const double* r, double* z, int mem, void* stream);
+
+/* The stable sort of the points: perm[i] = original index of the i-th sorted
+ * point and key[i] its Morton key (either pointer may be NULL); n entries. */
+SPS_API int sps_get_sort(sps_plan* plan, int64_t* perm, uint64_t* key, int mem, void* stream);
+
+/* Jacobi damping omega_g for g = 1..G (omega[g-1]); host memory. */
+SPS_API int sps_get_omega(const sps_plan* plan, double* omega);
+
+/* Override omega_g (host array of G values, all > 0). */
+SPS_API int sps_set_omega(sps_plan* plan, const double* omega);
+
+/* Kernel timing of the point operator (the dominant kernel): between
+ * sps_profile_begin and sps_profile_end every launch of the point operator in
+ * its apply mode is bracketed by CUDA events on its stream (at most 8192
+ * launches are timed).  sps_profile_end synchronises those events and returns
+ * the summed duration in ms and the number of timed launches. */
+SPS_API int sps_profile_begin(void);
+SPS_API int sps_profile_end(double* point_apply_ms, uint64_t* point_apply_launches);
+
+/* Number of CUDA kernels this library has launched in this process so far. */
+SPS_API int sps_launch_count(uint64_t* count);
+
+/* Timing probe: measured FMA throughput of the device in FMA/s for FP32
+ * (fp=0) or FP64 (fp=1), from a register-resident FMA loop over all SMs. */
+SPS_API int sps_probe_fma_rate(int fp, double* fma_per_s, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPS_H */

@@ -1,0 +1,1083 @@
+// C ABI, plan lifecycle, set-up pipeline, the V-cycle (Algorithm 7) and the
+// outer PCG (Algorithm 8, FP64) or its mixed-precision flexible variant.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "sps_internal.h"
+
+namespace sps {
+
+static thread_local std::string g_last_error = "no error";
+static std::atomic<unsigned long long> g_launches{0};
+
+void count_launches(unsigned long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+int cuda_fail(cudaError_t e, const char* what) {
+  g_last_error = std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e);
+  return SPS_ECUDA;
+}
+
+namespace {
+
+// scalar slots in plan->scal
+constexpr int S_RZ_A = 0, S_PV = 2, S_RR = 3, S_W = 4, S_FLAG = 6, S_RZ_B = 8, S_TMP = 10, S_TMP2 = 12;
+constexpr int NSCAL = 16;
+
+// ---- exact 1-D Gram matrices of the cubic B-splines --------------------------
+// Piece m of the uniform cubic B-spline on one cell, as monomial coefficients
+// in the local coordinate t: basis function (cell + m) restricted to the cell.
+const double kPiece[4][4] = {{1.0 / 6, -3.0 / 6, 3.0 / 6, -1.0 / 6},
+                             {4.0 / 6, 0.0, -6.0 / 6, 3.0 / 6},
+                             {1.0 / 6, 3.0 / 6, 3.0 / 6, -3.0 / 6},
+                             {0.0, 0.0, 0.0, 1.0 / 6}};
+
+// E_r[a][b] = int_0^1 d^r piece_a * d^r piece_b dt, exact (monomial integrals).
+void element_matrix(int r, double E[4][4]) {
+  double d[4][4];
+  for (int m = 0; m < 4; ++m) {
+    double c[4];
+    for (int k = 0; k < 4; ++k) c[k] = kPiece[m][k];
+    for (int s = 0; s < r; ++s) {
+      for (int k = 0; k < 3; ++k) c[k] = (k + 1) * c[k + 1];
+      c[3] = 0.0;
+    }
+    for (int k = 0; k < 4; ++k) d[m][k] = c[k];
+  }
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) {
+      double s = 0.0;
+      for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) s += d[a][i] * d[b][j] / (double)(i + j + 1);
+      E[a][b] = s;
+    }
+}
+
+// Band of Psi_r on [lo, hi] with N cells: band[j][o + q] = Psi_r[j, j + o].
+// The Gram matrix is the sum over the cells of the domain of the element
+// matrix (Section 2.4, Gramian of the r-th derivatives), scaled by h^(1-2r).
+void gram_band(int N, double h, int r, double* band) {
+  double E[4][4];
+  element_matrix(r, E);
+  const double sc = std::pow(h, 1.0 - 2.0 * r);
+  const int J = N + Q;
+  for (int j = 0; j < J; ++j)
+    for (int o = -Q; o <= Q; ++o) {
+      const int l = j + o;
+      double s = 0.0;
+      if (l >= 0 && l < J) {
+        const int c0 = std::max(0, std::max(j - Q, l - Q));
+        const int c1 = std::min(N - 1, std::min(j, l));
+        for (int c = c0; c <= c1; ++c) s += E[j - c][l - c];
+      }
+      band[(long long)j * BAND + o + Q] = s * sc;
+    }
+}
+
+template <typename T>
+void free_vecs(LevelVecs<T>& v) {
+  cudaFree(v.alpha);
+  cudaFree(v.b);
+  cudaFree(v.u);
+  cudaFree(v.dinv);
+  cudaFree(v.band);
+  v = LevelVecs<T>();
+}
+
+void free_points(sps_plan* pl) {
+  cudaFree(pl->x_sorted);
+  cudaFree(pl->y_sorted);
+  cudaFree(pl->keys);
+  cudaFree(pl->keys_tmp);
+  cudaFree(pl->perm);
+  cudaFree(pl->perm_tmp);
+  pl->x_sorted = nullptr;
+  pl->y_sorted = nullptr;
+  pl->keys = pl->keys_tmp = nullptr;
+  pl->perm = pl->perm_tmp = nullptr;
+  pl->n_cap = 0;
+}
+
+template <typename T>
+int alloc(T** p, long long count) {
+  if (count < 1) count = 1;
+  if (cudaMalloc((void**)p, sizeof(T) * count) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("device allocation failed");
+    return SPS_ENOMEM;
+  }
+  return SPS_OK;
+}
+
+#define SPS_TRY(x)          \
+  do {                      \
+    int _r = (x);           \
+    if (_r != SPS_OK) return _r; \
+  } while (0)
+
+__global__ void k_hash_fill(double* x, long long n, unsigned long long seed) {
+  // SplitMix64 (Steele, Lea, Flood 2014) in counter mode, mapped to [-1, 1).
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    unsigned long long z = seed + (unsigned long long)(i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    x[i] = (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+  }
+}
+
+__global__ void k_sqrt_copy(double* out, const double* in, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = sqrt(in[i]);
+}
+
+// x = y / sqrt(scal[slot])
+__global__ void k_normalize(double* x, const double* y, long long n, const double* scal, int slot) {
+  const double s = 1.0 / sqrt(scal[slot]);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    x[i] = y[i] * s;
+}
+
+__global__ void k_mul(double* out, const double* a, const double* b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = a[i] * b[i];
+}
+
+template <typename T>
+__global__ void k_fma_probe(T* out, int iters, T seed) {
+  T a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = seed + T(k) * T(1e-3) + T(threadIdx.x) * T(1e-7);
+  const T m = T(0.999999), c = T(1e-6);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = fma(a[k], m, c);
+  }
+  T s = T(0);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += a[k];
+  if (s == T(-12345)) out[0] = s;   // keeps the loop alive
+}
+
+cudaStream_t as_stream(void* s) { return (cudaStream_t)s; }
+
+long long max_K(const sps_plan* pl) {
+  long long m = 0;
+  for (int g = 0; g < pl->G; ++g) m = std::max(m, pl->lev[g].geom.K);
+  return m;
+}
+
+int read_scalars(sps_plan* pl, cudaStream_t st) {
+  SPS_CUDA(cudaMemcpyAsync(pl->host_scal, pl->scal, sizeof(double) * NSCAL, cudaMemcpyDeviceToHost, st));
+  SPS_CUDA(cudaStreamSynchronize(st));
+  return SPS_OK;
+}
+
+int copy_in(double* dst, const double* src, long long n, int mem, cudaStream_t st) {
+  SPS_CUDA(cudaMemcpyAsync(dst, src, sizeof(double) * n,
+                           mem == SPS_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
+  return SPS_OK;
+}
+
+int copy_out(double* dst, const double* src, long long n, int mem, cudaStream_t st) {
+  SPS_CUDA(cudaMemcpyAsync(dst, src, sizeof(double) * n,
+                           mem == SPS_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+  if (mem == SPS_MEM_HOST) SPS_CUDA(cudaStreamSynchronize(st));
+  return SPS_OK;
+}
+
+}  // namespace
+
+// ---- operator on one level: u = (Phi_g'Phi_g + lambda Lambda_g) v --------------
+template <typename T>
+int apply_level(sps_plan* pl, int g, const T* v, T* u, cudaStream_t st) {
+  SPS_TRY(penalty_apply<T>(pl, g, v, u, pl->lam, st));    // u = lambda Lambda v
+  return point_op<T>(pl, g, PT_APPLY, v, u, st);          // u += Phi'Phi v
+}
+template int apply_level<double>(sps_plan*, int, const double*, double*, cudaStream_t);
+template int apply_level<float>(sps_plan*, int, const float*, float*, cudaStream_t);
+
+// ---- Algorithm 7 from alpha = 0: xG = V(bG) -------------------------------------
+template <typename T>
+int vcycle_into(sps_plan* pl, const T* bG, T* xG, cudaStream_t st) {
+  const int G = pl->G;
+  const int nu1 = pl->opt.nu1, nu2 = pl->opt.nu2;
+  auto B = [&](int g) -> T* { return g == G ? const_cast<T*>(bG) : vecs<T>(pl->lev[g - 1]).b; };
+  auto X = [&](int g) -> T* { return g == G ? xG : vecs<T>(pl->lev[g - 1]).alpha; };
+  for (int g = G; g >= 2; --g) {
+    Level& L = pl->lev[g - 1];
+    LevelVecs<T>& V = vecs<T>(L);
+    const long long K = L.geom.K;
+    const T om = T(L.omega);
+    if (nu1 >= 1) {
+      SPS_TRY(vec_scale_mul<T>(X(g), V.dinv, B(g), om, K, st));        // first sweep from alpha = 0
+      for (int s = 1; s < nu1; ++s) {
+        SPS_TRY(apply_level<T>(pl, g, X(g), V.u, st));
+        SPS_TRY(vec_jacobi<T>(X(g), V.dinv, B(g), V.u, om, K, st));
+      }
+      SPS_TRY(apply_level<T>(pl, g, X(g), V.u, st));                  // r = A alpha - b
+    } else {
+      SPS_CUDA(cudaMemsetAsync(X(g), 0, sizeof(T) * K, st));
+      SPS_CUDA(cudaMemsetAsync(V.u, 0, sizeof(T) * K, st));
+    }
+    SPS_TRY(restrict_res<T>(pl, g, V.u, B(g), B(g - 1), st));         // b_{g-1} = I'(A alpha - b)
+  }
+  SPS_TRY(coarse_solve<T>(pl, B(1), X(1), st));                       // e = A_1^{-1} r
+  for (int g = 2; g <= G; ++g) {
+    Level& L = pl->lev[g - 1];
+    LevelVecs<T>& V = vecs<T>(L);
+    const long long K = L.geom.K;
+    const T om = T(L.omega);
+    SPS_TRY(prolong_sub<T>(pl, g, X(g - 1), X(g), 1, st));            // alpha <- alpha - I e
+    for (int s = 0; s < nu2; ++s) {
+      SPS_TRY(apply_level<T>(pl, g, X(g), V.u, st));
+      SPS_TRY(vec_jacobi<T>(X(g), V.dinv, B(g), V.u, om, K, st));
+    }
+  }
+  return SPS_OK;
+}
+
+namespace {
+
+// Largest eigenvalue of D_g^-1 A_g by power iteration on D^-1/2 A D^-1/2
+// (FP32 operator, FP64 vectors); omega_g = 4 / (3 lambda_max).
+int estimate_omega(sps_plan* pl, int g, cudaStream_t st) {
+  Level& L = pl->lev[g - 1];
+  const long long K = L.geom.K;
+  const int blocks = grid_blocks(K, 256);
+  double* x = L.d.alpha;
+  double* y = L.d.u;
+  double* s = L.d.b;
+  k_sqrt_copy<<<blocks, 256, 0, st>>>(s, L.d.dinv, K);
+  k_hash_fill<<<blocks, 256, 0, st>>>(x, K, 0x5EEDull + (unsigned long long)g);
+  SPS_CHECK_LAUNCH("power init");
+  SPS_TRY(dot(pl, x, x, K, S_TMP, st));
+  k_normalize<<<blocks, 256, 0, st>>>(x, x, K, pl->scal, S_TMP);
+  const int iters = std::max(pl->opt.power_iters, 1);
+  for (int it = 0; it < iters; ++it) {
+    k_mul<<<blocks, 256, 0, st>>>(y, s, x, K);
+    SPS_TRY(vec_cast_d2f(L.f.alpha, y, K, st));
+    SPS_TRY(apply_level<float>(pl, g, L.f.alpha, L.f.u, st));
+    SPS_TRY(vec_cast_f2d(y, L.f.u, K, st));
+    k_mul<<<blocks, 256, 0, st>>>(y, s, y, K);
+    SPS_TRY(dot(pl, x, y, K, S_TMP2, st));       // Rayleigh quotient (|x| = 1)
+    SPS_TRY(dot(pl, y, y, K, S_TMP, st));
+    k_normalize<<<blocks, 256, 0, st>>>(x, y, K, pl->scal, S_TMP);
+    SPS_CHECK_LAUNCH("power step");
+  }
+  SPS_TRY(read_scalars(pl, st));
+  const double lmax = pl->host_scal[S_TMP2];
+  if (!(lmax > 0.0) || !std::isfinite(lmax)) {
+    set_error("power iteration for the Jacobi damping failed");
+    return SPS_EBREAKDOWN;
+  }
+  L.omega = 4.0 / (3.0 * lmax);
+  return SPS_OK;
+}
+
+int check_plan_points(const sps_plan* pl) {
+  if (!pl) {
+    set_error("null plan");
+    return SPS_EINVAL;
+  }
+  if (!pl->have_points) {
+    set_error("sps_set_points has not been called");
+    return SPS_ESTATE;
+  }
+  return SPS_OK;
+}
+
+int solve_fp64(sps_plan* pl, double tol, sps_result* res, bool warm, cudaStream_t st) {
+  const int G = pl->G;
+  const long long K = pl->lev[G - 1].geom.K;
+  const double nb = pl->rhs_norm;
+  int rz = S_RZ_A, rz_next = S_RZ_B;
+  int it = 0;
+  int status = SPS_OK;
+  double rel = 1.0;
+  auto restart = [&](bool have_x) -> int {
+    if (have_x) {
+      SPS_TRY(apply_level<double>(pl, G, pl->x, pl->v, st));
+      SPS_TRY(vec_residual(pl->r, pl->rhs, pl->v, K, pl->scal, S_RR, pl, st));
+      res->fp64_applies++;
+    } else {
+      SPS_CUDA(cudaMemsetAsync(pl->x, 0, sizeof(double) * K, st));
+      SPS_CUDA(cudaMemcpyAsync(pl->r, pl->rhs, sizeof(double) * K, cudaMemcpyDeviceToDevice, st));
+      SPS_TRY(dot(pl, pl->r, pl->r, K, S_RR, st));
+    }
+    SPS_TRY(vcycle_into<double>(pl, pl->r, pl->z, st));
+    SPS_CUDA(cudaMemcpyAsync(pl->p, pl->z, sizeof(double) * K, cudaMemcpyDeviceToDevice, st));
+    SPS_TRY(dot(pl, pl->r, pl->z, K, rz, st));
+    SPS_TRY(read_scalars(pl, st));
+    rel = std::sqrt(pl->host_scal[S_RR]) / nb;
+    return SPS_OK;
+  };
+  SPS_CUDA(cudaMemsetAsync(pl->scal, 0, sizeof(double) * NSCAL, st));
+  SPS_TRY(restart(warm));
+  for (int round = 0; round < 4; ++round) {
+    while (rel > tol && it < pl->opt.max_iter) {
+      SPS_TRY(apply_level<double>(pl, G, pl->p, pl->v, st));       // v = A p
+      res->fp64_applies++;
+      SPS_TRY(dot(pl, pl->p, pl->v, K, S_PV, st));                  // p'v
+      SPS_TRY(pcg_update_xr(pl, K, rz, st));                        // alpha += w p, r -= w v
+      SPS_TRY(read_scalars(pl, st));
+      ++it;
+      if (pl->host_scal[S_FLAG] != 0.0) {
+        status = SPS_EBREAKDOWN;
+        break;
+      }
+      rel = std::sqrt(pl->host_scal[S_RR]) / nb;
+      if (rel <= tol) break;
+      SPS_TRY(vcycle_into<double>(pl, pl->r, pl->z, st));          // z = V(r)
+      SPS_TRY(dot(pl, pl->r, pl->z, K, rz_next, st));
+      SPS_TRY(pcg_update_p(pl, K, rz_next, rz, 0, st));             // p = z + (r'z / r~'z~) p
+      std::swap(rz, rz_next);
+    }
+    if (status != SPS_OK) break;
+    // true residual in FP64; iterate on if the recursion drifted
+    SPS_TRY(apply_level<double>(pl, G, pl->x, pl->v, st));
+    SPS_TRY(vec_residual(pl->z, pl->rhs, pl->v, K, pl->scal, S_TMP, pl, st));
+    SPS_TRY(read_scalars(pl, st));
+    res->rel_res_true = std::sqrt(pl->host_scal[S_TMP]) / nb;
+    if (res->rel_res_true <= tol || it >= pl->opt.max_iter) break;
+    SPS_TRY(restart(true));
+  }
+  res->iterations = it;
+  res->rel_res = rel;
+  if (status == SPS_OK && res->rel_res_true > tol) status = SPS_ENOCONV;
+  res->status = status;
+  return status;
+}
+
+// Flexible PCG (Polak-Ribiere beta, Notay 2000) in FP64 with the FP32 V-cycle
+// and FP32 point operator; the FP64 residual b - A alpha is recomputed when
+// the recursive residual has dropped by replace_ratio (reliable updates).
+int solve_mixed(sps_plan* pl, double tol, sps_result* res, bool warm, cudaStream_t st) {
+  const int G = pl->G;
+  Level& LG = pl->lev[G - 1];
+  const long long K = LG.geom.K;
+  const double nb = pl->rhs_norm;
+  float* a32 = LG.f.alpha;
+  float* v32 = pl->ftmp[7];      // the apply does not use ftmp[6..7]
+  int it = 0, status = SPS_OK;
+  double rel = 1.0, rlast = 0.0;
+  const double ratio = pl->opt.replace_ratio > 0 ? pl->opt.replace_ratio : 1e-2;
+  SPS_CUDA(cudaMemsetAsync(pl->scal, 0, sizeof(double) * NSCAL, st));
+  if (warm) {
+    SPS_TRY(apply_level<double>(pl, G, pl->x, pl->v, st));
+    SPS_TRY(vec_residual(pl->r, pl->rhs, pl->v, K, pl->scal, S_RR, pl, st));
+    res->fp64_applies++;
+  } else {
+    SPS_CUDA(cudaMemsetAsync(pl->x, 0, sizeof(double) * K, st));
+    SPS_CUDA(cudaMemcpyAsync(pl->r, pl->rhs, sizeof(double) * K, cudaMemcpyDeviceToDevice, st));
+    SPS_TRY(dot(pl, pl->r, pl->r, K, S_RR, st));
+  }
+  auto precondition = [&]() -> int {          // z = V32(r)
+    SPS_TRY(vec_cast_d2f(LG.f.b, pl->r, K, st));
+    SPS_TRY(vcycle_into<float>(pl, LG.f.b, a32, st));
+    return vec_cast_f2d(pl->z, a32, K, st);
+  };
+  SPS_TRY(precondition());
+  SPS_CUDA(cudaMemcpyAsync(pl->p, pl->z, sizeof(double) * K, cudaMemcpyDeviceToDevice, st));
+  SPS_TRY(dot(pl, pl->r, pl->z, K, S_RZ_A, st));
+  SPS_TRY(read_scalars(pl, st));
+  rel = std::sqrt(pl->host_scal[S_RR]) / nb;
+  rlast = std::sqrt(pl->host_scal[S_RR]);
+  while (rel > tol && it < pl->opt.max_iter) {
+    SPS_TRY(vec_cast_d2f(pl->p32, pl->p, K, st));
+    SPS_TRY(apply_level<float>(pl, G, pl->p32, v32, st));            // v = A p (FP32 operator)
+    SPS_TRY(vec_cast_f2d(pl->v, v32, K, st));
+    SPS_TRY(dot(pl, pl->p, pl->v, K, S_PV, st));
+    SPS_CUDA(cudaMemcpyAsync(pl->rprev, pl->r, sizeof(double) * K, cudaMemcpyDeviceToDevice, st));
+    SPS_TRY(pcg_update_xr(pl, K, S_RZ_A, st));
+    SPS_TRY(read_scalars(pl, st));
+    ++it;
+    if (pl->host_scal[S_FLAG] != 0.0) {
+      status = SPS_EBREAKDOWN;
+      break;
+    }
+    double rn = std::sqrt(pl->host_scal[S_RR]);
+    rel = rn / nb;
+    if (rel <= tol || rn <= ratio * rlast) {                         // FP64 residual replacement
+      SPS_TRY(apply_level<double>(pl, G, pl->x, pl->v, st));
+      SPS_TRY(vec_residual(pl->r, pl->rhs, pl->v, K, pl->scal, S_RR, pl, st));
+      SPS_TRY(read_scalars(pl, st));
+      res->fp64_applies++;
+      rn = std::sqrt(pl->host_scal[S_RR]);
+      rel = rn / nb;
+      rlast = rn;
+      if (rel <= tol) break;
+    }
+    SPS_TRY(precondition());
+    SPS_TRY(dot2(pl, pl->z, pl->r, pl->rprev, K, S_RZ_B, st));      // z'r, z'r_prev
+    SPS_TRY(pcg_update_p(pl, K, S_RZ_B, S_RZ_A, 1, st));            // beta = z'(r - r_prev) / r~'z~
+    SPS_CUDA(cudaMemcpyAsync(pl->scal + S_RZ_A, pl->scal + S_RZ_B, sizeof(double), cudaMemcpyDeviceToDevice, st));
+  }
+  res->iterations = it;
+  res->rel_res = rel;
+  // final FP64 check (the loop exits right after a replacement when converged)
+  SPS_TRY(apply_level<double>(pl, G, pl->x, pl->v, st));
+  SPS_TRY(vec_residual(pl->z, pl->rhs, pl->v, K, pl->scal, S_TMP, pl, st));
+  SPS_TRY(read_scalars(pl, st));
+  res->rel_res_true = std::sqrt(pl->host_scal[S_TMP]) / nb;
+  if (status == SPS_OK && res->rel_res_true > tol) status = SPS_ENOCONV;
+  res->status = status;
+  return status;
+}
+
+// Temporary device copies of double vectors for the component entry points.
+struct DevBuf {
+  void* p = nullptr;
+  ~DevBuf() { if (p) cudaFree(p); }
+};
+
+int stage_in(const double* src, long long n, int mem, DevBuf& buf, const double** dev, cudaStream_t st) {
+  if (mem == SPS_MEM_DEVICE) {
+    *dev = src;
+    return SPS_OK;
+  }
+  SPS_TRY(alloc((double**)&buf.p, n));
+  SPS_CUDA(cudaMemcpyAsync(buf.p, src, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+  *dev = (const double*)buf.p;
+  return SPS_OK;
+}
+
+int stage_out_ptr(double* dst, long long n, int mem, DevBuf& buf, double** dev) {
+  if (mem == SPS_MEM_DEVICE) {
+    *dev = dst;
+    return SPS_OK;
+  }
+  SPS_TRY(alloc((double**)&buf.p, n));
+  *dev = (double*)buf.p;
+  return SPS_OK;
+}
+
+int finish_out(double* dst, const double* dev, long long n, int mem, cudaStream_t st) {
+  if (mem == SPS_MEM_DEVICE) return SPS_OK;
+  return copy_out(dst, dev, n, SPS_MEM_HOST, st);
+}
+
+int check_level(const sps_plan* pl, int level, int lowest) {
+  if (level < lowest || level > pl->G) {
+    set_error("level out of range");
+    return SPS_EINVAL;
+  }
+  return SPS_OK;
+}
+
+// Run a float kernel on double inputs: widen/narrow through temporaries.
+template <typename F>
+int run_f32(long long nin, long long nout, const double* in, double* out, F&& fn, cudaStream_t st) {
+  DevBuf a, b;
+  SPS_TRY(alloc((float**)&a.p, nin));
+  SPS_TRY(alloc((float**)&b.p, nout));
+  SPS_TRY(vec_cast_d2f((float*)a.p, in, nin, st));
+  SPS_TRY(fn((const float*)a.p, (float*)b.p));
+  SPS_TRY(vec_cast_f2d(out, (const float*)b.p, nout, st));
+  SPS_CUDA(cudaStreamSynchronize(st));
+  return SPS_OK;
+}
+
+}  // namespace
+}  // namespace sps
+
+using namespace sps;
+
+extern "C" {
+
+void sps_default_options(sps_options* opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->precision = SPS_PREC_FP64;
+  opt->nu1 = 1;
+  opt->nu2 = 1;
+  opt->omega = 0.0;
+  opt->power_iters = 20;
+  opt->max_iter = 500;
+  opt->warm_start = 0;
+  opt->tile = 0;
+  opt->replace_ratio = 1e-2;
+}
+
+const char* sps_last_error(void) { return g_last_error.c_str(); }
+
+int sps_plan_create(sps_plan** out, int P, int q, const int* intervals, const double* lo, const double* hi,
+                    int levels, double lambda, const sps_options* opt) {
+  if (!out || !intervals) {
+    set_error("null argument");
+    return SPS_EINVAL;
+  }
+  *out = nullptr;
+  if (P < 1 || P > MAXP) {
+    set_error("P must be in 1..5");
+    return SPS_EINVAL;
+  }
+  if (q != Q) {
+    set_error("only cubic splines (q = 3) are built");
+    return SPS_EINVAL;
+  }
+  if (levels < 1 || levels > MAXL) {
+    set_error("levels must be in 1..12");
+    return SPS_EINVAL;
+  }
+  if (!(lambda >= 0.0) || !std::isfinite(lambda)) {
+    set_error("lambda must be finite and >= 0");
+    return SPS_EINVAL;
+  }
+  sps_options o;
+  sps_default_options(&o);
+  if (opt) o = *opt;
+  if (o.nu1 < 0 || o.nu2 < 0 || o.max_iter < 1 || (o.precision != SPS_PREC_FP64 && o.precision != SPS_PREC_MIXED) ||
+      o.tile < 0 || (o.tile & (o.tile - 1)) != 0) {
+    set_error("invalid options");
+    return SPS_EINVAL;
+  }
+  int Lbits = 1;
+  for (int p = 0; p < P; ++p) {
+    const int N = intervals[p];
+    if (N < 1 || (N & (N - 1)) != 0 || N > 4096) {
+      set_error("intervals must be powers of two <= 4096");
+      return SPS_EINVAL;
+    }
+    if ((N >> (levels - 1)) < 1) {
+      set_error("too many levels for the grid: the coarsest level needs >= 1 interval");
+      return SPS_EINVAL;
+    }
+    int b = 0;
+    while ((1 << b) < N) ++b;
+    Lbits = std::max(Lbits, b);
+    const double l = lo ? lo[p] : 0.0, h = hi ? hi[p] : 1.0;
+    if (!std::isfinite(l) || !std::isfinite(h) || !(h > l)) {
+      set_error("domain bounds must be finite with lo < hi");
+      return SPS_EINVAL;
+    }
+  }
+  if (P * Lbits > 26) {
+    set_error("grid too fine for the cell index (P * log2(max N) must be <= 26)");
+    return SPS_EINVAL;
+  }
+  sps_plan* pl = new (std::nothrow) sps_plan();
+  if (!pl) {
+    set_error("host allocation failed");
+    return SPS_ENOMEM;
+  }
+  pl->P = P;
+  pl->q = q;
+  pl->G = levels;
+  pl->lam = lambda;
+  pl->opt = o;
+  pl->Lbits = Lbits;
+  cudaGetDevice(&pl->device);
+  for (int p = 0; p < P; ++p) {
+    pl->N[p] = intervals[p];
+    pl->lo[p] = lo ? lo[p] : 0.0;
+    pl->hi[p] = hi ? hi[p] : 1.0;
+  }
+  const int ts_default[6] = {0, 256, 32, 8, 4, 2};
+  int rc = SPS_OK;
+  for (int g = 1; g <= levels && rc == SPS_OK; ++g) {
+    LevelGeom& G = pl->lev[g - 1].geom;
+    G = LevelGeom();
+    G.P = P;
+    G.shift = levels - g;
+    G.ts = o.tile > 0 ? o.tile : ts_default[P];
+    G.K = 1;
+    for (int p = P - 1; p >= 0; --p) {
+      G.N[p] = intervals[p] >> (levels - g);
+      G.J[p] = G.N[p] + Q;
+      G.stride[p] = G.K;
+      G.K *= G.J[p];
+      G.lo[p] = pl->lo[p];
+      G.inv_h[p] = (double)G.N[p] / (pl->hi[p] - pl->lo[p]);
+      G.E[p] = std::min(G.ts, G.N[p]) + Q;
+    }
+    int es = 1;
+    for (int p = P - 1; p >= 0; --p) {
+      G.Es[p] = es;
+      es *= G.E[p];
+    }
+    G.patch = es;
+    if (g == 1 && G.K > COARSE_MAX) {
+      set_error("coarsest level too large for the dense coarse solve (K_1 > 4096): add levels");
+      rc = SPS_EINVAL;
+    }
+    if ((long long)G.patch * 8 * 2 > 200 * 1024) {
+      set_error("tile too large for shared memory");
+      rc = SPS_EINVAL;
+    }
+  }
+  if (rc != SPS_OK) {
+    delete pl;
+    return rc;
+  }
+  // per-level vectors and Gram bands
+  std::vector<double> hb;
+  for (int g = 1; g <= levels && rc == SPS_OK; ++g) {
+    Level& L = pl->lev[g - 1];
+    const LevelGeom& G = L.geom;
+    long long nb = 0;
+    for (int p = 0; p < P; ++p) nb += 3LL * G.J[p] * BAND;
+    hb.assign(nb, 0.0);
+    long long off = 0;
+    for (int p = 0; p < P; ++p) {
+      const double h = (pl->hi[p] - pl->lo[p]) / G.N[p];
+      for (int r = 0; r < 3; ++r) gram_band(G.N[p], h, r, hb.data() + off + (long long)r * G.J[p] * BAND);
+      off += 3LL * G.J[p] * BAND;
+    }
+    std::vector<float> hf(hb.begin(), hb.end());
+    if ((rc = alloc(&L.d.alpha, G.K)) || (rc = alloc(&L.d.b, G.K)) || (rc = alloc(&L.d.u, G.K)) ||
+        (rc = alloc(&L.d.dinv, G.K)) || (rc = alloc(&L.d.band, nb)) || (rc = alloc(&L.f.alpha, G.K)) ||
+        (rc = alloc(&L.f.b, G.K)) || (rc = alloc(&L.f.u, G.K)) || (rc = alloc(&L.f.dinv, G.K)) ||
+        (rc = alloc(&L.f.band, nb)) || (rc = alloc(&L.diag, G.K)))
+      break;
+    if (cudaMemcpy(L.d.band, hb.data(), sizeof(double) * nb, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(L.f.band, hf.data(), sizeof(float) * nb, cudaMemcpyHostToDevice) != cudaSuccess) {
+      set_error("copy of Gram bands failed");
+      rc = SPS_ECUDA;
+    }
+  }
+  const long long KG = pl->lev[levels - 1].geom.K;
+  const long long K1 = pl->lev[0].geom.K;
+  const long long Km = max_K(pl);
+  for (int i = 0; i < 8 && rc == SPS_OK; ++i) {
+    rc = alloc(&pl->dtmp[i], Km);
+    if (rc == SPS_OK) rc = alloc(&pl->ftmp[i], Km);
+  }
+  if (rc == SPS_OK)
+    if ((rc = alloc(&pl->x, KG)) || (rc = alloc(&pl->r, KG)) || (rc = alloc(&pl->z, KG)) ||
+        (rc = alloc(&pl->p, KG)) || (rc = alloc(&pl->v, KG)) || (rc = alloc(&pl->rprev, KG)) ||
+        (rc = alloc(&pl->p32, KG)) || (rc = alloc(&pl->rhs, KG)) || (rc = alloc(&pl->coarse_inv, K1 * K1)) ||
+        (rc = alloc(&pl->coarse_inv_f, K1 * K1)) || (rc = alloc(&pl->coarse_tmp, 4 * K1)) ||
+        (rc = alloc(&pl->scal, NSCAL)) || (rc = alloc(&pl->red_part, 4 * 304)) ||
+        (rc = alloc(&pl->red_count, 1)) || (rc = alloc(&pl->err_flag, 1))) {
+    }
+  if (rc == SPS_OK) {
+    if (cudaMemset(pl->red_count, 0, sizeof(unsigned int)) != cudaSuccess ||
+        cudaMallocHost((void**)&pl->host_scal, sizeof(double) * NSCAL) != cudaSuccess) {
+      set_error("initialisation failed");
+      rc = SPS_ECUDA;
+    }
+  }
+  if (rc != SPS_OK) {
+    sps_destroy(pl);
+    return rc;
+  }
+  *out = pl;
+  return SPS_OK;
+}
+
+int sps_destroy(sps_plan* pl) {
+  if (!pl) return SPS_OK;
+  for (int g = 0; g < MAXL; ++g) {
+    Level& L = pl->lev[g];
+    free_vecs(L.d);
+    free_vecs(L.f);
+    cudaFree(L.diag);
+    cudaFree(L.run_begin);
+    cudaFree(L.run_cell);
+    cudaFree(L.items);
+  }
+  free_points(pl);
+  for (int i = 0; i < 8; ++i) {
+    cudaFree(pl->dtmp[i]);
+    cudaFree(pl->ftmp[i]);
+  }
+  cudaFree(pl->x);
+  cudaFree(pl->r);
+  cudaFree(pl->z);
+  cudaFree(pl->p);
+  cudaFree(pl->v);
+  cudaFree(pl->rprev);
+  cudaFree(pl->p32);
+  cudaFree(pl->rhs);
+  cudaFree(pl->coarse_inv);
+  cudaFree(pl->coarse_inv_f);
+  cudaFree(pl->coarse_tmp);
+  cudaFree(pl->scal);
+  cudaFree(pl->red_part);
+  cudaFree(pl->red_count);
+  cudaFree(pl->err_flag);
+  cudaFree(pl->sort_hist);
+  cudaFree(pl->seg_tmp);
+  if (pl->host_scal) cudaFreeHost(pl->host_scal);
+  delete pl;
+  return SPS_OK;
+}
+
+int sps_set_points(sps_plan* pl, int64_t n, const void* x, const void* y, int dtype, int mem, void* stream) {
+  if (!pl || !x || !y) {
+    set_error("null argument");
+    return SPS_EINVAL;
+  }
+  if (n == 0) {
+    set_error("no data points");
+    return SPS_EEMPTY;
+  }
+  if (n < 0 || n >= (1LL << 31) - 1 || (dtype != SPS_F32 && dtype != SPS_F64) ||
+      (mem != SPS_MEM_HOST && mem != SPS_MEM_DEVICE)) {
+    set_error("invalid n, dtype or mem");
+    return SPS_EINVAL;
+  }
+  cudaStream_t st = as_stream(stream);
+  pl->have_points = false;
+  const int P = pl->P;
+  const size_t es = dtype == SPS_F64 ? 8 : 4;
+  if (n > pl->n_cap || dtype != pl->dtype) {
+    free_points(pl);
+    int rc;
+    if ((rc = alloc((char**)&pl->x_sorted, (long long)es * P * n)) || (rc = alloc(&pl->y_sorted, n)) ||
+        (rc = alloc(&pl->keys, n)) || (rc = alloc(&pl->keys_tmp, n)) || (rc = alloc(&pl->perm, n)) ||
+        (rc = alloc(&pl->perm_tmp, n))) {
+      free_points(pl);
+      return rc;
+    }
+    pl->n_cap = n;
+  }
+  pl->n = n;
+  pl->dtype = dtype;
+  // device copies of host inputs
+  DevBuf hx, hy;
+  const void* xd = x;
+  const void* yd = y;
+  if (mem == SPS_MEM_HOST) {
+    SPS_TRY(alloc((char**)&hx.p, (long long)es * P * n));
+    SPS_TRY(alloc((char**)&hy.p, (long long)es * n));
+    SPS_CUDA(cudaMemcpyAsync(hx.p, x, es * P * n, cudaMemcpyHostToDevice, st));
+    SPS_CUDA(cudaMemcpyAsync(hy.p, y, es * n, cudaMemcpyHostToDevice, st));
+    xd = hx.p;
+    yd = hy.p;
+  }
+  SPS_TRY(compute_keys(pl, xd, dtype, st));
+  int bad = 0;
+  SPS_CUDA(cudaMemcpyAsync(&bad, pl->err_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SPS_CUDA(cudaStreamSynchronize(st));
+  if (bad) {
+    set_error("a point lies outside [lo, hi] or is not finite");
+    return SPS_EDOM;
+  }
+  SPS_TRY(radix_sort(pl, P * pl->Lbits, st));
+  SPS_TRY(gather_points(pl, xd, yd, dtype, st));
+  for (int g = 1; g <= pl->G; ++g) SPS_TRY(build_level_work(pl, g, st));
+  // right-hand side Phi'y (Algorithm 3 with the responses)
+  const int G = pl->G;
+  const long long KG = pl->lev[G - 1].geom.K;
+  SPS_CUDA(cudaMemsetAsync(pl->rhs, 0, sizeof(double) * KG, st));
+  SPS_TRY(point_op<double>(pl, G, PT_RHS, nullptr, pl->rhs, st));
+  SPS_TRY(dot(pl, pl->rhs, pl->rhs, KG, S_TMP, st));
+  // diag(A_g) = diag(Phi_g'Phi_g) (Algorithm 5) + lambda diag(Lambda_g)
+  for (int g = 1; g <= G; ++g) {
+    Level& L = pl->lev[g - 1];
+    SPS_CUDA(cudaMemsetAsync(L.diag, 0, sizeof(double) * L.geom.K, st));
+    SPS_TRY(point_op<double>(pl, g, PT_DIAG, nullptr, L.diag, st));
+    SPS_TRY(penalty_diag(pl, g, L.diag, st));
+    SPS_TRY(vec_recip(L.d.dinv, L.f.dinv, L.diag, L.geom.K, st));
+  }
+  SPS_TRY(read_scalars(pl, st));
+  pl->rhs_norm = std::sqrt(pl->host_scal[S_TMP]);
+  SPS_TRY(coarse_assemble(pl, st));
+  for (int g = 2; g <= G; ++g) {
+    if (pl->opt.omega > 0.0) pl->lev[g - 1].omega = pl->opt.omega;
+    else SPS_TRY(estimate_omega(pl, g, st));
+  }
+  pl->lev[0].omega = pl->opt.omega > 0.0 ? pl->opt.omega : 0.0;
+  SPS_CUDA(cudaStreamSynchronize(st));
+  SPS_CUDA(cudaGetLastError());
+  pl->have_points = true;
+  return SPS_OK;
+}
+
+int sps_solve(sps_plan* pl, double* coef, int mem, double tol, sps_result* res_out, void* stream) {
+  SPS_TRY(check_plan_points(pl));
+  if (!coef || !(tol > 0.0) || (mem != SPS_MEM_HOST && mem != SPS_MEM_DEVICE)) {
+    set_error("invalid coef, tol or mem");
+    return SPS_EINVAL;
+  }
+  cudaStream_t st = as_stream(stream);
+  auto t0 = std::chrono::steady_clock::now();
+  sps_result res;
+  std::memset(&res, 0, sizeof(res));
+  const long long KG = pl->lev[pl->G - 1].geom.K;
+  if (pl->rhs_norm == 0.0) {   // y = 0: alpha = 0
+    SPS_CUDA(cudaMemsetAsync(pl->x, 0, sizeof(double) * KG, st));
+    res.status = SPS_OK;
+  } else {
+    const bool warm = pl->opt.warm_start != 0;
+    if (warm) SPS_TRY(copy_in(pl->x, coef, KG, mem, st));
+    int rc = pl->opt.precision == SPS_PREC_MIXED ? solve_mixed(pl, tol, &res, warm, st)
+                                                 : solve_fp64(pl, tol, &res, warm, st);
+    if (rc != SPS_OK && rc != SPS_ENOCONV && rc != SPS_EBREAKDOWN) return rc;
+    if (rc == SPS_EBREAKDOWN) set_error("CG breakdown (p'Ap <= 0 or non-finite)");
+    if (rc == SPS_ENOCONV) set_error("max_iter reached before the tolerance");
+  }
+  SPS_TRY(copy_out(coef, pl->x, KG, mem, st));
+  SPS_CUDA(cudaStreamSynchronize(st));
+  res.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (res_out) *res_out = res;
+  return res.status;
+}
+
+int sps_coef_count(const sps_plan* pl, int level, int64_t* K) {
+  if (!pl || !K) {
+    set_error("null argument");
+    return SPS_EINVAL;
+  }
+  SPS_TRY(check_level(pl, level, 1));
+  *K = pl->lev[level - 1].geom.K;
+  return SPS_OK;
+}
+
+int sps_apply(sps_plan* pl, int level, int prec, const double* v, double* u, int mem, void* stream) {
+  SPS_TRY(check_plan_points(pl));
+  SPS_TRY(check_level(pl, level, 1));
+  cudaStream_t st = as_stream(stream);
+  const long long K = pl->lev[level - 1].geom.K;
+  DevBuf bi, bo;
+  const double* vd;
+  double* ud;
+  SPS_TRY(stage_in(v, K, mem, bi, &vd, st));
+  SPS_TRY(stage_out_ptr(u, K, mem, bo, &ud));
+  if (prec == SPS_PREC_MIXED) {
+    SPS_TRY(run_f32(K, K, vd, ud, [&](const float* a, float* b) { return apply_level<float>(pl, level, a, b, st); },
+                    st));
+  } else {
+    SPS_TRY(apply_level<double>(pl, level, vd, ud, st));
+  }
+  return finish_out(u, ud, K, mem, st);
+}
+
+int sps_point_apply(sps_plan* pl, int level, int prec, const double* v, double* u, int mem, void* stream) {
+  SPS_TRY(check_plan_points(pl));
+  SPS_TRY(check_level(pl, level, 1));
+  cudaStream_t st = as_stream(stream);
+  const long long K = pl->lev[level - 1].geom.K;
+  DevBuf bi, bo;
+  const double* vd;
+  double* ud;
+  SPS_TRY(stage_in(v, K, mem, bi, &vd, st));
+  SPS_TRY(stage_out_ptr(u, K, mem, bo, &ud));
+  if (prec == SPS_PREC_MIXED) {
+    SPS_TRY(run_f32(K, K, vd, ud,
+                    [&](const float* a, float* b) {
+                      SPS_CUDA(cudaMemsetAsync(b, 0, sizeof(float) * K, st));
+                      return point_op<float>(pl, level, PT_APPLY, a, b, st);
+                    },
+                    st));
+  } else {
+    SPS_CUDA(cudaMemsetAsync(ud, 0, sizeof(double) * K, st));
+    SPS_TRY(point_op<double>(pl, level, PT_APPLY, vd, ud, st));
+  }
+  return finish_out(u, ud, K, mem, st);
+}
+
+int sps_profile_begin(void) { return profile_begin(); }
+
+int sps_profile_end(double* point_apply_ms, uint64_t* point_apply_launches) {
+  if (!point_apply_ms || !point_apply_launches) {
+    set_error("null argument");
+    return SPS_EINVAL;
+  }
+  unsigned long long l = 0;
+  SPS_TRY(profile_end(point_apply_ms, &l));
+  *point_apply_launches = l;
+  return SPS_OK;
+}
+
+int sps_launch_count(uint64_t* count) {
+  if (!count) {
+    set_error("null argument");
+    return SPS_EINVAL;
+  }
+  *count = g_launches.load();
+  return SPS_OK;
+}
+
+int sps_penalty_apply(sps_plan* pl, int level, int prec, const double* v, double* u, int mem, void* stream) {
+  SPS_TRY(check_plan_points(pl));
+  SPS_TRY(check_level(pl, level, 1));
+  cudaStream_t st = as_stream(stream);
+  const long long K = pl->lev[level - 1].geom.K;
+  DevBuf bi, bo;
+  const double* vd;
+  double* ud;
+  SPS_TRY(stage_in(v, K, mem, bi, &vd, st));
+  SPS_TRY(stage_out_ptr(u, K, mem, bo, &ud));
+  if (prec == SPS_PREC_MIXED) {
+    SPS_TRY(run_f32(K, K, vd, ud,
+                    [&](const float* a, float* b) { return penalty_apply<float>(pl, level, a, b, 1.0, st); }, st));
+  } else {
+    SPS_TRY(penalty_apply<double>(pl, level, vd, ud, 1.0, st));
+  }
+  return finish_out(u, ud, K, mem, st);
+}
+
+int sps_diag(sps_plan* pl, int level, double* d, int mem, void* stream) {
+  SPS_TRY(check_plan_points(pl));
+  SPS_TRY(check_level(pl, level, 1));
+  cudaStream_t st = as_stream(stream);
+  return copy_out(d, pl->lev[level - 1].diag, pl->lev[level - 1].geom.K, mem, st);
+}
+
+int sps_rhs(sps_plan* pl, double* b, int mem, void* stream) {
+  SPS_TRY(check_plan_points(pl));
+  return copy_out(b, pl->rhs, pl->lev[pl->G - 1].geom.K, mem, as_stream(stream));
+}
+
+int sps_prolong(sps_plan* pl, int level, int prec, const double* c, double* f, int mem, void* stream) {
+  SPS_TRY(check_plan_points(pl));
+  SPS_TRY(check_level(pl, level, 2));
+  cudaStream_t st = as_stream(stream);
+  const long long Kc = pl->lev[level - 2].geom.K, Kf = pl->lev[level - 1].geom.K;
+  DevBuf bi, bo;
+  const double* cd;
+  double* fd;
+  SPS_TRY(stage_in(c, Kc, mem, bi, &cd, st));
+  SPS_TRY(stage_out_ptr(f, Kf, mem, bo, &fd));
+  if (prec == SPS_PREC_MIXED) {
+    SPS_TRY(run_f32(Kc, Kf, cd, fd, [&](const float* a, float* b) { return prolong_sub<float>(pl, level, a, b, 0, st); },
+                    st));
+  } else {
+    SPS_TRY(prolong_sub<double>(pl, level, cd, fd, 0, st));
+  }
+  return finish_out(f, fd, Kf, mem, st);
+}
+
+int sps_restrict(sps_plan* pl, int level, int prec, const double* f, double* c, int mem, void* stream) {
+  SPS_TRY(check_plan_points(pl));
+  SPS_TRY(check_level(pl, level, 2));
+  cudaStream_t st = as_stream(stream);
+  const long long Kc = pl->lev[level - 2].geom.K, Kf = pl->lev[level - 1].geom.K;
+  DevBuf bi, bo;
+  const double* fd;
+  double* cd;
+  SPS_TRY(stage_in(f, Kf, mem, bi, &fd, st));
+  SPS_TRY(stage_out_ptr(c, Kc, mem, bo, &cd));
+  if (prec == SPS_PREC_MIXED) {
+    SPS_TRY(run_f32(Kf, Kc, fd, cd,
+                    [&](const float* a, float* b) { return restrict_res<float>(pl, level, a, nullptr, b, st); }, st));
+  } else {
+    SPS_TRY(restrict_res<double>(pl, level, fd, nullptr, cd, st));
+  }
+  return finish_out(c, cd, Kc, mem, st);
+}
+
+int sps_coarse_solve(sps_plan* pl, const double* r, double* e, int mem, void* stream) {
+  SPS_TRY(check_plan_points(pl));
+  cudaStream_t st = as_stream(stream);
+  const long long K = pl->lev[0].geom.K;
+  DevBuf bi, bo;
+  const double* rd;
+  double* ed;
+  SPS_TRY(stage_in(r, K, mem, bi, &rd, st));
+  SPS_TRY(stage_out_ptr(e, K, mem, bo, &ed));
+  SPS_TRY(coarse_solve<double>(pl, rd, ed, st));
+  return finish_out(e, ed, K, mem, st);
+}
+
+int sps_vcycle(sps_plan* pl, int prec, const double* r, double* z, int mem, void* stream) {
+  SPS_TRY(check_plan_points(pl));
+  cudaStream_t st = as_stream(stream);
+  const int G = pl->G;
+  const long long K = pl->lev[G - 1].geom.K;
+  DevBuf bi, bo;
+  const double* rd;
+  double* zd;
+  SPS_TRY(stage_in(r, K, mem, bi, &rd, st));
+  SPS_TRY(stage_out_ptr(z, K, mem, bo, &zd));
+  if (prec == SPS_PREC_MIXED) {
+    Level& LG = pl->lev[G - 1];
+    SPS_TRY(vec_cast_d2f(LG.f.b, rd, K, st));
+    SPS_TRY(vcycle_into<float>(pl, LG.f.b, LG.f.alpha, st));
+    SPS_TRY(vec_cast_f2d(zd, LG.f.alpha, K, st));
+  } else {
+    SPS_CUDA(cudaMemcpyAsync(pl->r, rd, sizeof(double) * K, cudaMemcpyDeviceToDevice, st));
+    SPS_TRY(vcycle_into<double>(pl, pl->r, zd, st));
+  }
+  SPS_CUDA(cudaStreamSynchronize(st));
+  return finish_out(z, zd, K, mem, st);
+}
+
+int sps_get_sort(sps_plan* pl, int64_t* perm, uint64_t* key, int mem, void* stream) {
+  SPS_TRY(check_plan_points(pl));
+  cudaStream_t st = as_stream(stream);
+  const long long n = pl->n;
+  if (key) {
+    SPS_CUDA(cudaMemcpyAsync(key, pl->keys, sizeof(uint64_t) * n,
+                             mem == SPS_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+  }
+  if (perm) {
+    // widen the 32-bit permutation on the host side of the copy
+    std::vector<unsigned int> h(n);
+    SPS_CUDA(cudaMemcpyAsync(h.data(), pl->perm, sizeof(unsigned int) * n, cudaMemcpyDeviceToHost, st));
+    SPS_CUDA(cudaStreamSynchronize(st));
+    std::vector<int64_t> w(h.begin(), h.end());
+    SPS_CUDA(cudaMemcpyAsync(perm, w.data(), sizeof(int64_t) * n,
+                             mem == SPS_MEM_HOST ? cudaMemcpyHostToHost : cudaMemcpyHostToDevice, st));
+  }
+  SPS_CUDA(cudaStreamSynchronize(st));
+  return SPS_OK;
+}
+
+int sps_get_omega(const sps_plan* pl, double* omega) {
+  if (!pl || !omega) {
+    set_error("null argument");
+    return SPS_EINVAL;
+  }
+  for (int g = 0; g < pl->G; ++g) omega[g] = pl->lev[g].omega;
+  return SPS_OK;
+}
+
+int sps_set_omega(sps_plan* pl, const double* omega) {
+  if (!pl || !omega) {
+    set_error("null argument");
+    return SPS_EINVAL;
+  }
+  for (int g = 0; g < pl->G; ++g)
+    if (!(omega[g] > 0.0) || !std::isfinite(omega[g])) {
+      set_error("omega must be positive");
+      return SPS_EINVAL;
+    }
+  for (int g = 0; g < pl->G; ++g) pl->lev[g].omega = omega[g];
+  return SPS_OK;
+}
+
+int sps_probe_fma_rate(int fp, double* fma_per_s, void* stream) {
+  if (!fma_per_s) {
+    set_error("null argument");
+    return SPS_EINVAL;
+  }
+  cudaStream_t st = as_stream(stream);
+  int dev = 0, sms = 0;
+  SPS_CUDA(cudaGetDevice(&dev));
+  SPS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  DevBuf out;
+  SPS_TRY(alloc((double**)&out.p, 1));
+  const int threads = 256, blocks = sms * 8;
+  const int iters = fp ? 4000 : 100000;
+  cudaEvent_t e0, e1;
+  SPS_CUDA(cudaEventCreate(&e0));
+  SPS_CUDA(cudaEventCreate(&e1));
+  float ms = 0.0f;
+  for (int rep = 0; rep < 2; ++rep) {   // first launch warms up
+    SPS_CUDA(cudaEventRecord(e0, st));
+    if (fp) k_fma_probe<double><<<blocks, threads, 0, st>>>((double*)out.p, iters, 1.0);
+    else k_fma_probe<float><<<blocks, threads, 0, st>>>((float*)out.p, iters, 1.0f);
+    SPS_CUDA(cudaEventRecord(e1, st));
+    SPS_CUDA(cudaEventSynchronize(e1));
+    SPS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *fma_per_s = (double)blocks * threads * iters * 8.0 / (ms * 1e-3);
+  return SPS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,707 @@
+// Coefficient-space kernels: the penalty Lambda v through its Kronecker-sum
+// structure, the subdivision prolongation and its transpose, the coarse
+// matrix and its inverse, the elementwise smoother updates and the fused PCG
+// vector updates with their dot products.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "sps_internal.h"
+
+namespace sps {
+
+namespace {
+
+constexpr int EW_THREADS = 256;
+constexpr int RED_BLOCKS = 304;      // 2 per SM; fixed so reductions are deterministic
+
+// ------------------------------------------------------------------ penalty
+// Lambda = sum_{|r|=2} (2/r!) kron_p Psi^p_{r_p} (Section 2.2, Section 2.4).
+// Dimension by dimension (Algorithm 2 applies one Kronecker factor per mode)
+// three partial sums are carried: W0 (all factors Psi_0 so far), W1 (exactly
+// one Psi_1), W2 (derivative order two, weighted by 2/r!):
+//   W0' = M W0,  W1' = M W1 + D1 W0,  W2' = M W2 + 2 D1 W1 + D2 W0,
+// with M = Psi^p_0, D1 = Psi^p_1, D2 = Psi^p_2 banded (2q+1 diagonals).
+// stage: 0 first dimension, 1 middle, 2 last, 3 only dimension.
+template <typename T>
+__global__ void k_pen_sweep(int stage, long long K, long long strd, int Jp, const T* __restrict__ band,
+                            const T* __restrict__ w0, const T* __restrict__ w1, const T* __restrict__ w2,
+                            T* __restrict__ o0, T* __restrict__ o1, T* __restrict__ o2, T scale) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < K;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)((k / strd) % Jp);
+    const T* M = band + (long long)j * BAND;
+    const T* D1 = band + ((long long)Jp + j) * BAND;
+    const T* D2 = band + (2LL * Jp + j) * BAND;
+    T a0 = T(0), a1 = T(0), a2 = T(0);
+#pragma unroll
+    for (int o = -Q; o <= Q; ++o) {
+      const int jj = j + o;
+      if (jj < 0 || jj >= Jp) continue;
+      const long long kk = k + (long long)o * strd;
+      const T m = M[o + Q], d1 = D1[o + Q], d2 = D2[o + Q];
+      if (stage == 0) {
+        const T x = w0[kk];
+        a0 = fma(m, x, a0);
+        a1 = fma(d1, x, a1);
+        a2 = fma(d2, x, a2);
+      } else if (stage == 3) {
+        a2 = fma(d2, w0[kk], a2);
+      } else {
+        const T x0 = w0[kk], x1 = w1[kk], x2 = w2[kk];
+        if (stage == 1) {
+          a0 = fma(m, x0, a0);
+          a1 = fma(m, x1, fma(d1, x0, a1));
+        }
+        a2 = fma(m, x2, fma(T(2) * d1, x1, fma(d2, x0, a2)));
+      }
+    }
+    if (stage <= 1) {
+      o0[k] = a0;
+      o1[k] = a1;
+      o2[k] = a2;
+    } else {
+      o2[k] = scale * a2;
+    }
+  }
+}
+
+// diag(Lambda) by the same recursion on the central band entries.
+__global__ void k_pen_diag(long long K, LevelGeom geom, const double* __restrict__ band, double lam,
+                           double* __restrict__ d, int accumulate) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < K;
+       k += (long long)gridDim.x * blockDim.x) {
+    double d0 = 1.0, d1 = 0.0, d2 = 0.0;
+    long long boff = 0;
+    for (int p = 0; p < geom.P; ++p) {
+      const int Jp = geom.J[p];
+      const int j = (int)((k / geom.stride[p]) % Jp);
+      const double m = band[boff + (long long)j * BAND + Q];
+      const double e1 = band[boff + ((long long)Jp + j) * BAND + Q];
+      const double e2 = band[boff + (2LL * Jp + j) * BAND + Q];
+      d2 = m * d2 + 2.0 * e1 * d1 + e2 * d0;
+      d1 = m * d1 + e1 * d0;
+      d0 = m * d0;
+      boff += 3LL * Jp * BAND;
+    }
+    d[k] = (accumulate ? d[k] : 0.0) + lam * d2;
+  }
+}
+
+// ------------------------------------------------------------------ transfers
+// 1-D subdivision weights 2^-q binom(q+1, k), k = i - 2j + q (Section 2.4).
+__constant__ double c_subdiv[Q + 2] = {1.0 / 8, 4.0 / 8, 6.0 / 8, 4.0 / 8, 1.0 / 8};
+
+// out (fine along the swept mode) = I_1d * in (coarse along it).
+template <typename T>
+__global__ void k_prolong_sweep(long long Kout, long long inner, int Jin, int Jout, const T* __restrict__ in,
+                                T* __restrict__ out, int subtract) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < Kout;
+       k += (long long)gridDim.x * blockDim.x) {
+    const long long outer = k / ((long long)Jout * inner);
+    const long long rem = k - outer * Jout * inner;
+    const int i = (int)(rem / inner);
+    const long long ii = rem - (long long)i * inner;
+    T s = T(0);
+#pragma unroll
+    for (int kk = 0; kk <= Q + 1; ++kk) {
+      const int num = i + Q - kk;
+      if (num & 1) continue;
+      const int j = num >> 1;
+      if (j < 0 || j >= Jin) continue;
+      s = fma(T(c_subdiv[kk]), in[(outer * Jin + j) * inner + ii], s);
+    }
+    if (subtract) out[k] -= s; else out[k] = s;
+  }
+}
+
+// out (coarse along the mode) = I_1d' * (in - inb) (fine along it).
+template <typename T>
+__global__ void k_restrict_sweep(long long Kout, long long inner, int Jin, int Jout, const T* __restrict__ in,
+                                 const T* __restrict__ inb, T* __restrict__ out) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < Kout;
+       k += (long long)gridDim.x * blockDim.x) {
+    const long long outer = k / ((long long)Jout * inner);
+    const long long rem = k - outer * Jout * inner;
+    const int j = (int)(rem / inner);
+    const long long ii = rem - (long long)j * inner;
+    T s = T(0);
+#pragma unroll
+    for (int kk = 0; kk <= Q + 1; ++kk) {
+      const int i = 2 * j - Q + kk;
+      if (i < 0 || i >= Jin) continue;
+      const long long src = (outer * Jin + i) * inner + ii;
+      const T val = inb ? in[src] - inb[src] : in[src];
+      s = fma(T(c_subdiv[kk]), val, s);
+    }
+    out[k] = s;
+  }
+}
+
+// ------------------------------------------------------------------ coarse matrix
+// A_1 = Phi_1'Phi_1 + lambda Lambda_1, assembled densely (Section 3.2, coarse
+// grid solver).  One CTA takes a contiguous range of runs (points of one cell)
+// and a block of CB local columns; each thread owns 16 entries of the local
+// (q+1)^P x CB block of sum_i b_i b_i' in FP64 registers.  Products use TP.
+template <int P, typename TP>
+__global__ void __launch_bounds__(256) k_coarse_phi(const int* __restrict__ run_begin,
+                                                    const unsigned long long* __restrict__ run_cell, int nruns,
+                                                    int runs_per_cta, const void* __restrict__ xs_raw, int x_f64,
+                                                    long long n, LevelGeom geom, double* __restrict__ A1) {
+  constexpr int LOC = 1 << (2 * P);
+  constexpr int CB = P <= 3 ? LOC : (P == 4 ? 16 : 4);
+  constexpr int PER = (LOC * CB + 255) / 256;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TP* B = reinterpret_cast<TP*>(smem_raw);                 // [RUN_MAX][LOC]
+  TP* bas = B + RUN_MAX * LOC;                              // [RUN_MAX][P][4]
+  const int cb0 = blockIdx.y * CB;
+  double acc[PER];
+  TP part[PER];
+#pragma unroll
+  for (int e = 0; e < PER; ++e) acc[e] = 0.0;
+  const int r0 = blockIdx.x * runs_per_cta;
+  const int r1 = min(r0 + runs_per_cta, nruns);
+  unsigned long long cur = ~0ull;
+  auto flush = [&](unsigned long long cell) {
+    int c[MAXP];
+    for (int p = 0; p < P; ++p) c[p] = (int)((cell >> (12 * p)) & 0xFFF);
+#pragma unroll
+    for (int e = 0; e < PER; ++e) {
+      const int le = threadIdx.x + 256 * e;
+      if (le >= LOC * CB) break;
+      const int row = le / CB, col = le % CB + cb0;
+      long long gr = 0, gc = 0;
+      int rr = row, cc = col;
+      for (int p = P - 1; p >= 0; --p) {
+        gr += (long long)(c[p] + (rr & 3)) * geom.stride[p];
+        gc += (long long)(c[p] + (cc & 3)) * geom.stride[p];
+        rr >>= 2;
+        cc >>= 2;
+      }
+      if (acc[e] != 0.0) atomicAdd(&A1[gr * geom.K + gc], acc[e]);
+      acc[e] = 0.0;
+    }
+  };
+  for (int r = r0; r < r1; ++r) {
+    const unsigned long long cell = run_cell[r];
+    if (cell != cur) {
+      if (cur != ~0ull) flush(cur);
+      cur = cell;
+    }
+    const int i0 = run_begin[r], i1 = run_begin[r + 1];
+    const int np = i1 - i0;
+    __syncthreads();
+    for (int e = threadIdx.x; e < np * P; e += blockDim.x) {
+      const int i = e / P, p = e % P;
+      const double xv = x_f64 ? ((const double*)xs_raw)[(long long)p * n + i0 + i]
+                              : (double)((const float*)xs_raw)[(long long)p * n + i0 + i];
+      const int c = (int)((cell >> (12 * p)) & 0xFFF);
+      const double t = xv * geom.inv_h[p] - (geom.lo[p] * geom.inv_h[p] + (double)c);
+      const double om = 1.0 - t, t2 = t * t;
+      TP* b = bas + (i * P + p) * 4;
+      b[0] = TP(om * om * om / 6.0);
+      b[1] = TP(t2 * (0.5 * t - 1.0) + 2.0 / 3.0);
+      b[2] = TP(((-0.5 * t + 0.5) * t + 0.5) * t + 1.0 / 6.0);
+      b[3] = TP(t2 * t / 6.0);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < np * LOC; e += blockDim.x) {
+      const int i = e / LOC, l = e % LOC;
+      TP v = TP(1);
+      int ll = l;
+      for (int p = P - 1; p >= 0; --p) {
+        v *= bas[(i * P + p) * 4 + (ll & 3)];
+        ll >>= 2;
+      }
+      B[i * LOC + l] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < PER; ++e) part[e] = TP(0);
+    for (int i = 0; i < np; ++i) {
+#pragma unroll
+      for (int e = 0; e < PER; ++e) {
+        const int le = threadIdx.x + 256 * e;
+        if (le >= LOC * CB) break;
+        const int row = le / CB, col = le % CB + cb0;
+        part[e] = fma(B[i * LOC + row], B[i * LOC + col], part[e]);
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < PER; ++e) acc[e] += (double)part[e];
+  }
+  if (cur != ~0ull) flush(cur);
+}
+
+// + lambda Lambda_1 on the stencil neighbourhood of every row.
+__global__ void k_coarse_penalty(LevelGeom geom, const double* __restrict__ band, double lam,
+                                 double* __restrict__ A1) {
+  const long long K = geom.K;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < K * K;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long k = e / K, l = e % K;
+    double d0 = 1.0, d1 = 0.0, d2 = 0.0;
+    long long boff = 0;
+    bool nz = true;
+    for (int p = 0; p < geom.P && nz; ++p) {
+      const int Jp = geom.J[p];
+      const int j = (int)((k / geom.stride[p]) % Jp);
+      const int jl = (int)((l / geom.stride[p]) % Jp);
+      const int o = jl - j;
+      if (o < -Q || o > Q) { nz = false; break; }
+      const double m = band[boff + (long long)j * BAND + o + Q];
+      const double e1 = band[boff + ((long long)Jp + j) * BAND + o + Q];
+      const double e2 = band[boff + (2LL * Jp + j) * BAND + o + Q];
+      d2 = m * d2 + 2.0 * e1 * d1 + e2 * d0;
+      d1 = m * d1 + e1 * d0;
+      d0 = m * d0;
+      boff += 3LL * Jp * BAND;
+    }
+    if (nz) A1[e] += lam * d2;
+  }
+}
+
+// In-place Gauss-Jordan inversion of the SPD coarse matrix, one pivot per
+// launch.  rowk/colk hold row and column k as they were before step k; the
+// threads that write row/column k+1 also record them for the next step.
+__global__ void k_gj_init(const double* __restrict__ A, long long K, double* __restrict__ rowk,
+                          double* __restrict__ colk) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < K; i += (long long)gridDim.x * blockDim.x) {
+    rowk[i] = A[i];
+    colk[i] = A[i * K];
+  }
+}
+
+__global__ void k_gj_step(double* __restrict__ A, long long K, int k, const double* __restrict__ rowk,
+                          const double* __restrict__ colk, double* __restrict__ rown, double* __restrict__ coln) {
+  const double piv = rowk[k];
+  const double ipiv = 1.0 / piv;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < K * K;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e / K, j = e % K;
+    double a;
+    if (i == k && j == k) a = ipiv;
+    else if (i == k) a = rowk[j] * ipiv;
+    else if (j == k) a = -colk[i] * ipiv;
+    else a = A[e] - colk[i] * rowk[j] * ipiv;
+    A[e] = a;
+    if (i == k + 1) rown[j] = a;
+    if (j == k + 1) coln[i] = a;
+  }
+}
+
+__global__ void k_f64_to_f32(const double* __restrict__ a, float* __restrict__ b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+
+// e = A_1^{-1} r, one warp per row, FP64 arithmetic.
+template <typename T>
+__global__ void k_gemv(const double* __restrict__ Ainv, long long K, const T* __restrict__ r, T* __restrict__ e) {
+  const int lane = threadIdx.x & 31;
+  for (long long row = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; row < K;
+       row += ((long long)gridDim.x * blockDim.x) >> 5) {
+    double s = 0.0;
+    for (long long c = lane; c < K; c += 32) s = fma(Ainv[row * K + c], (double)r[c], s);
+    for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) e[row] = T(s);
+  }
+}
+
+// ------------------------------------------------------------------ elementwise
+template <typename T>
+__global__ void k_scale_mul(T* __restrict__ out, const T* __restrict__ a, const T* __restrict__ b, T s, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = s * a[i] * b[i];
+}
+
+// Algorithm 6: alpha <- alpha + omega D^-1 (b - A alpha), with u = A alpha.
+template <typename T>
+__global__ void k_jacobi(T* __restrict__ alpha, const T* __restrict__ dinv, const T* __restrict__ b,
+                         const T* __restrict__ u, T omega, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    alpha[i] = fma(omega * dinv[i], b[i] - u[i], alpha[i]);
+}
+
+__global__ void k_cast_d2f(float* __restrict__ o, const double* __restrict__ a, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    o[i] = (float)a[i];
+}
+__global__ void k_cast_f2d(double* __restrict__ o, const float* __restrict__ a, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    o[i] = (double)a[i];
+}
+template <typename T>
+__global__ void k_set(T* __restrict__ o, T v, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    o[i] = v;
+}
+__global__ void k_recip(double* __restrict__ dinv, float* __restrict__ dinv_f, const double* __restrict__ d,
+                        long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double v = 1.0 / d[i];
+    dinv[i] = v;
+    if (dinv_f) dinv_f[i] = (float)v;
+  }
+}
+
+// ------------------------------------------------------------------ reductions
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < 32) {
+    t = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o >= 1; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  }
+  return t;   // valid in thread 0
+}
+
+// Last-block reduction of NV per-block partials (fixed order: deterministic).
+template <int NV>
+__device__ __forceinline__ bool finish_reduction(const double* vals, double* part, unsigned int* count,
+                                                 double* out, double* sh) {
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < NV; ++q) part[q * gridDim.x + blockIdx.x] = vals[q];
+    __threadfence();
+    const unsigned int t = atomicAdd(count, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  for (int q = 0; q < NV; ++q) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s += *((volatile double*)&part[q * gridDim.x + b]);
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) out[q] = s;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *count = 0;
+  return true;
+}
+
+__global__ void k_dot(const double* __restrict__ a, const double* __restrict__ b, const double* __restrict__ c,
+                      long long n, double* part, unsigned int* count, double* out) {
+  __shared__ double sh[32];
+  double s0 = 0.0, s1 = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double av = a[i];
+    s0 = fma(av, b[i], s0);
+    if (c) s1 = fma(av, c[i], s1);
+  }
+  double v[2];
+  v[0] = block_sum(s0, sh);
+  __syncthreads();
+  v[1] = c ? block_sum(s1, sh) : 0.0;
+  finish_reduction<2>(v, part, count, out, sh);
+}
+
+// Algorithm 8: w = rz / p'v; alpha += w p; r -= w v; and |r|^2.
+// scal layout: [rz_slot] r'z, [2] p'v, [3] r'r (out), [4] w (out), [6] flag.
+__global__ void k_update_xr(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
+                            const double* __restrict__ v, long long n, double* scal, int rz_slot, double* part,
+                            unsigned int* count) {
+  __shared__ double sh[32];
+  const double pv = scal[2];
+  const double w = scal[rz_slot] / pv;
+  const bool bad = !(pv > 0.0) || !isfinite(w);
+  double s = 0.0;
+  if (!bad) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+      x[i] = fma(w, p[i], x[i]);
+      const double ri = fma(-w, v[i], r[i]);
+      r[i] = ri;
+      s = fma(ri, ri, s);
+    }
+  }
+  double vals[1];
+  vals[0] = block_sum(s, sh);
+  if (finish_reduction<1>(vals, part, count, scal + 3, sh) && threadIdx.x == 0) {
+    scal[4] = w;
+    if (bad) scal[6] = 1.0;
+  }
+}
+
+// p = z + beta p with beta = num / den (flexible: (num - num2) / den).
+__global__ void k_update_p(double* __restrict__ p, const double* __restrict__ z, long long n, const double* scal,
+                           int num_slot, int den_slot, int flexible) {
+  double beta = scal[num_slot];
+  if (flexible) beta -= scal[num_slot + 1];
+  beta /= scal[den_slot];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    p[i] = fma(beta, p[i], z[i]);
+}
+
+__global__ void k_residual(double* __restrict__ r, const double* __restrict__ b, const double* __restrict__ u,
+                           long long n, double* part, unsigned int* count, double* out) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double ri = b[i] - u[i];
+    r[i] = ri;
+    s = fma(ri, ri, s);
+  }
+  double vals[1];
+  vals[0] = block_sum(s, sh);
+  finish_reduction<1>(vals, part, count, out, sh);
+}
+
+template <typename T>
+T* tmp_of(sps_plan* pl, int i);
+template <>
+double* tmp_of<double>(sps_plan* pl, int i) { return pl->dtmp[i]; }
+template <>
+float* tmp_of<float>(sps_plan* pl, int i) { return pl->ftmp[i]; }
+
+}  // namespace
+
+// ------------------------------------------------------------------ host wrappers
+template <typename T>
+int penalty_apply(sps_plan* pl, int g, const T* v, T* out, double scale, cudaStream_t st) {
+  Level& L = pl->lev[g - 1];
+  const LevelGeom& G = L.geom;
+  const int P = pl->P;
+  const T* band = vecs<T>(L).band;
+  const int blocks = grid_blocks(G.K, EW_THREADS);
+  if (P == 1) {
+    k_pen_sweep<T><<<blocks, EW_THREADS, 0, st>>>(3, G.K, G.stride[0], G.J[0], band, v, nullptr, nullptr, nullptr,
+                                                   nullptr, out, T(scale));
+    SPS_CHECK_LAUNCH("penalty");
+    return SPS_OK;
+  }
+  T* A[3] = {tmp_of<T>(pl, 0), tmp_of<T>(pl, 1), tmp_of<T>(pl, 2)};
+  T* B[3] = {tmp_of<T>(pl, 3), tmp_of<T>(pl, 4), tmp_of<T>(pl, 5)};
+  long long boff = 0;
+  for (int p = 0; p < P; ++p) {
+    const T* bp = band + boff;
+    if (p == 0) {
+      k_pen_sweep<T><<<blocks, EW_THREADS, 0, st>>>(0, G.K, G.stride[p], G.J[p], bp, v, nullptr, nullptr, A[0], A[1],
+                                                     A[2], T(1));
+    } else if (p < P - 1) {
+      k_pen_sweep<T><<<blocks, EW_THREADS, 0, st>>>(1, G.K, G.stride[p], G.J[p], bp, A[0], A[1], A[2], B[0], B[1],
+                                                     B[2], T(1));
+      std::swap(A, B);
+    } else {
+      k_pen_sweep<T><<<blocks, EW_THREADS, 0, st>>>(2, G.K, G.stride[p], G.J[p], bp, A[0], A[1], A[2], nullptr,
+                                                     nullptr, out, T(scale));
+    }
+    SPS_CHECK_LAUNCH("penalty sweep");
+    boff += 3LL * G.J[p] * BAND;
+  }
+  return SPS_OK;
+}
+template int penalty_apply<double>(sps_plan*, int, const double*, double*, double, cudaStream_t);
+template int penalty_apply<float>(sps_plan*, int, const float*, float*, double, cudaStream_t);
+
+int penalty_diag(sps_plan* pl, int g, double* d, cudaStream_t st) {
+  Level& L = pl->lev[g - 1];
+  k_pen_diag<<<grid_blocks(L.geom.K, EW_THREADS), EW_THREADS, 0, st>>>(L.geom.K, L.geom, L.d.band, pl->lam, d, 1);
+  SPS_CHECK_LAUNCH("penalty diag");
+  return SPS_OK;
+}
+
+// f = I c (mode 0) or f -= I c (mode 1); c on level g-1, f on level g.
+template <typename T>
+int prolong_sub(sps_plan* pl, int g, const T* c, T* f, int mode, cudaStream_t st) {
+  const LevelGeom& Gf = pl->lev[g - 1].geom;
+  const LevelGeom& Gc = pl->lev[g - 2].geom;
+  const int P = pl->P;
+  T* tmp[2] = {tmp_of<T>(pl, 6), tmp_of<T>(pl, 7)};
+  const T* in = c;
+  for (int p = 0; p < P; ++p) {
+    long long inner = 1, outer = 1;
+    for (int q = p + 1; q < P; ++q) inner *= Gc.J[q];
+    for (int q = 0; q < p; ++q) outer *= Gf.J[q];
+    const long long Kout = outer * Gf.J[p] * inner;
+    const bool last = p == P - 1;
+    T* out = last ? f : tmp[p & 1];
+    k_prolong_sweep<T><<<grid_blocks(Kout, EW_THREADS), EW_THREADS, 0, st>>>(Kout, inner, Gc.J[p], Gf.J[p], in, out,
+                                                                              last ? mode : 0);
+    SPS_CHECK_LAUNCH("prolong");
+    in = out;
+  }
+  return SPS_OK;
+}
+template int prolong_sub<double>(sps_plan*, int, const double*, double*, int, cudaStream_t);
+template int prolong_sub<float>(sps_plan*, int, const float*, float*, int, cudaStream_t);
+
+// c = I' (f - fb) with f, fb on level g and c on level g-1.
+template <typename T>
+int restrict_res(sps_plan* pl, int g, const T* f, const T* fb, T* c, cudaStream_t st) {
+  const LevelGeom& Gf = pl->lev[g - 1].geom;
+  const LevelGeom& Gc = pl->lev[g - 2].geom;
+  const int P = pl->P;
+  T* tmp[2] = {tmp_of<T>(pl, 6), tmp_of<T>(pl, 7)};
+  const T* in = f;
+  const T* inb = fb;
+  for (int p = 0; p < P; ++p) {
+    long long inner = 1, outer = 1;
+    for (int q = p + 1; q < P; ++q) inner *= Gf.J[q];
+    for (int q = 0; q < p; ++q) outer *= Gc.J[q];
+    const long long Kout = outer * Gc.J[p] * inner;
+    T* out = p == P - 1 ? c : tmp[p & 1];
+    k_restrict_sweep<T><<<grid_blocks(Kout, EW_THREADS), EW_THREADS, 0, st>>>(Kout, inner, Gf.J[p], Gc.J[p], in, inb,
+                                                                               out);
+    SPS_CHECK_LAUNCH("restrict");
+    in = out;
+    inb = nullptr;
+  }
+  return SPS_OK;
+}
+template int restrict_res<double>(sps_plan*, int, const double*, const double*, double*, cudaStream_t);
+template int restrict_res<float>(sps_plan*, int, const float*, const float*, float*, cudaStream_t);
+
+template <int P>
+int coarse_phi_launch(sps_plan* pl, cudaStream_t st) {
+  Level& L = pl->lev[0];
+  constexpr int LOC = 1 << (2 * P);
+  constexpr int CB = P <= 3 ? LOC : (P == 4 ? 16 : 4);
+  const bool fp32 = pl->opt.precision == SPS_PREC_MIXED || P >= 4;
+  const int rpc = 8;
+  dim3 grid((L.nruns + rpc - 1) / rpc, LOC / CB);
+  if (L.nruns == 0) return SPS_OK;
+  if (fp32) {
+    const size_t smem = sizeof(float) * (RUN_MAX * LOC + RUN_MAX * P * 4);
+    SPS_CUDA(cudaFuncSetAttribute(k_coarse_phi<P, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    k_coarse_phi<P, float><<<grid, 256, smem, st>>>(L.run_begin, L.run_cell, L.nruns, rpc, pl->x_sorted,
+                                                   pl->dtype == SPS_F64, pl->n, L.geom, pl->coarse_inv);
+  } else {
+    const size_t smem = sizeof(double) * (RUN_MAX * LOC + RUN_MAX * P * 4);
+    SPS_CUDA(cudaFuncSetAttribute(k_coarse_phi<P, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    k_coarse_phi<P, double><<<grid, 256, smem, st>>>(L.run_begin, L.run_cell, L.nruns, rpc, pl->x_sorted,
+                                                    pl->dtype == SPS_F64, pl->n, L.geom, pl->coarse_inv);
+  }
+  SPS_CHECK_LAUNCH("coarse assembly");
+  return SPS_OK;
+}
+
+// Assemble A_1 into coarse_inv and invert it in place.
+int coarse_assemble(sps_plan* pl, cudaStream_t st) {
+  Level& L = pl->lev[0];
+  const long long K = L.geom.K;
+  SPS_CUDA(cudaMemsetAsync(pl->coarse_inv, 0, sizeof(double) * K * K, st));
+  int e = SPS_OK;
+  switch (pl->P) {
+    case 1: e = coarse_phi_launch<1>(pl, st); break;
+    case 2: e = coarse_phi_launch<2>(pl, st); break;
+    case 3: e = coarse_phi_launch<3>(pl, st); break;
+    case 4: e = coarse_phi_launch<4>(pl, st); break;
+    case 5: e = coarse_phi_launch<5>(pl, st); break;
+  }
+  if (e) return e;
+  k_coarse_penalty<<<grid_blocks(K * K, EW_THREADS), EW_THREADS, 0, st>>>(L.geom, L.d.band, pl->lam,
+                                                                          pl->coarse_inv);
+  SPS_CHECK_LAUNCH("coarse penalty");
+  double* rowk = pl->coarse_tmp;
+  double* colk = rowk + K;
+  double* rown = colk + K;
+  double* coln = rown + K;
+  k_gj_init<<<grid_blocks(K, EW_THREADS), EW_THREADS, 0, st>>>(pl->coarse_inv, K, rowk, colk);
+  SPS_CHECK_LAUNCH("gj init");
+  const int blocks = grid_blocks(K * K, EW_THREADS);
+  for (int k = 0; k < K; ++k) {
+    k_gj_step<<<blocks, EW_THREADS, 0, st>>>(pl->coarse_inv, K, k, rowk, colk, rown, coln);
+    std::swap(rowk, rown);
+    std::swap(colk, coln);
+  }
+  count_launches(K - 1);
+  SPS_CHECK_LAUNCH("gj step");
+  k_f64_to_f32<<<grid_blocks(K * K, EW_THREADS), EW_THREADS, 0, st>>>(pl->coarse_inv, pl->coarse_inv_f, K * K);
+  SPS_CHECK_LAUNCH("coarse cast");
+  return SPS_OK;
+}
+
+template <typename T>
+int coarse_solve(sps_plan* pl, const T* r, T* e, cudaStream_t st) {
+  const long long K = pl->lev[0].geom.K;
+  const int blocks = (int)std::min<long long>((K * 32 + EW_THREADS - 1) / EW_THREADS, 152LL * 16);
+  k_gemv<T><<<blocks, EW_THREADS, 0, st>>>(pl->coarse_inv, K, r, e);
+  SPS_CHECK_LAUNCH("coarse solve");
+  return SPS_OK;
+}
+template int coarse_solve<double>(sps_plan*, const double*, double*, cudaStream_t);
+template int coarse_solve<float>(sps_plan*, const float*, float*, cudaStream_t);
+
+template <typename T>
+int vec_scale_mul(T* out, const T* a, const T* b, T s, long long n, cudaStream_t st) {
+  k_scale_mul<T><<<grid_blocks(n, EW_THREADS), EW_THREADS, 0, st>>>(out, a, b, s, n);
+  SPS_CHECK_LAUNCH("scale mul");
+  return SPS_OK;
+}
+template int vec_scale_mul<double>(double*, const double*, const double*, double, long long, cudaStream_t);
+template int vec_scale_mul<float>(float*, const float*, const float*, float, long long, cudaStream_t);
+
+template <typename T>
+int vec_jacobi(T* alpha, const T* dinv, const T* b, const T* u, T omega, long long n, cudaStream_t st) {
+  k_jacobi<T><<<grid_blocks(n, EW_THREADS), EW_THREADS, 0, st>>>(alpha, dinv, b, u, omega, n);
+  SPS_CHECK_LAUNCH("jacobi");
+  return SPS_OK;
+}
+template int vec_jacobi<double>(double*, const double*, const double*, const double*, double, long long, cudaStream_t);
+template int vec_jacobi<float>(float*, const float*, const float*, const float*, float, long long, cudaStream_t);
+
+int vec_cast_d2f(float* out, const double* in, long long n, cudaStream_t st) {
+  k_cast_d2f<<<grid_blocks(n, EW_THREADS), EW_THREADS, 0, st>>>(out, in, n);
+  SPS_CHECK_LAUNCH("cast");
+  return SPS_OK;
+}
+int vec_cast_f2d(double* out, const float* in, long long n, cudaStream_t st) {
+  k_cast_f2d<<<grid_blocks(n, EW_THREADS), EW_THREADS, 0, st>>>(out, in, n);
+  SPS_CHECK_LAUNCH("cast");
+  return SPS_OK;
+}
+int vec_set_d(double* out, double v, long long n, cudaStream_t st) {
+  k_set<double><<<grid_blocks(n, EW_THREADS), EW_THREADS, 0, st>>>(out, v, n);
+  SPS_CHECK_LAUNCH("set");
+  return SPS_OK;
+}
+int vec_set_f(float* out, float v, long long n, cudaStream_t st) {
+  k_set<float><<<grid_blocks(n, EW_THREADS), EW_THREADS, 0, st>>>(out, v, n);
+  SPS_CHECK_LAUNCH("set");
+  return SPS_OK;
+}
+int vec_recip(double* dinv, float* dinv_f, const double* d, long long n, cudaStream_t st) {
+  k_recip<<<grid_blocks(n, EW_THREADS), EW_THREADS, 0, st>>>(dinv, dinv_f, d, n);
+  SPS_CHECK_LAUNCH("recip");
+  return SPS_OK;
+}
+
+int vec_residual(double* r, const double* b, const double* u, long long n, double* scal, int slot, sps_plan* pl,
+                 cudaStream_t st) {
+  k_residual<<<RED_BLOCKS, EW_THREADS, 0, st>>>(r, b, u, n, pl->red_part, pl->red_count, scal + slot);
+  SPS_CHECK_LAUNCH("residual");
+  return SPS_OK;
+}
+
+int dot(sps_plan* pl, const double* a, const double* b, long long n, int slot, cudaStream_t st) {
+  k_dot<<<RED_BLOCKS, EW_THREADS, 0, st>>>(a, b, nullptr, n, pl->red_part, pl->red_count, pl->scal + slot);
+  SPS_CHECK_LAUNCH("dot");
+  return SPS_OK;
+}
+
+int dot2(sps_plan* pl, const double* a, const double* b, const double* c, long long n, int slot, cudaStream_t st) {
+  k_dot<<<RED_BLOCKS, EW_THREADS, 0, st>>>(a, b, c, n, pl->red_part, pl->red_count, pl->scal + slot);
+  SPS_CHECK_LAUNCH("dot2");
+  return SPS_OK;
+}
+
+int pcg_update_xr(sps_plan* pl, long long n, int rz_slot, cudaStream_t st) {
+  k_update_xr<<<RED_BLOCKS, EW_THREADS, 0, st>>>(pl->x, pl->r, pl->p, pl->v, n, pl->scal, rz_slot, pl->red_part,
+                                                 pl->red_count);
+  SPS_CHECK_LAUNCH("update x r");
+  return SPS_OK;
+}
+
+int pcg_update_p(sps_plan* pl, long long n, int num_slot, int den_slot, int flexible, cudaStream_t st) {
+  k_update_p<<<grid_blocks(n, EW_THREADS), EW_THREADS, 0, st>>>(pl->p, pl->z, n, pl->scal, num_slot, den_slot,
+                                                                flexible);
+  SPS_CHECK_LAUNCH("update p");
+  return SPS_OK;
+}
+
+}  // namespace sps

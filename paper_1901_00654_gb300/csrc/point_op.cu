@@ -1,0 +1,321 @@
+// The point operator u += Phi_g'(Phi_g v) on one grid level (Section 3.2,
+// hierarchy: all n points on every level), fused from the transposed
+// Khatri-Rao product s_i = (kron_p Phi_p[i,.])' v (Algorithm 4) and the
+// Khatri-Rao product u = sum_i s_i kron_p Phi_p[i,.] (Algorithm 3), with the
+// (q+1)^P tensor-product basis values of each point formed on the fly from
+// its coordinates.  The same kernel with s_i = 1 and squared basis values
+// gives diag(Phi_g'Phi_g) (Algorithm 5), and with s_i = y_i the right-hand
+// side Phi'y (first line of Algorithm 8).
+//
+// Work decomposition (GB300 design, not the paper's loop order):
+//  * The points are sorted by cell, so the points of one level cell form a
+//    contiguous "run" (at most RUN_MAX points).  A CTA owns the runs of one
+//    tile of ts^P cells; the (ts+q)^P coefficients its points can touch are
+//    staged in shared memory.
+//  * A group of TPP = 4^(P-3) lanes (1 lane for P <= 3) takes one run at a
+//    time.  Each lane owns 64 (or 4^P) of the cell's (q+1)^P coefficients and
+//    keeps their partial sums in registers while it walks the run, so the
+//    scatter costs one shared-memory atomic per coefficient per run instead
+//    of one per point.  The gather is sum-factorised over the lane's last
+//    three dimensions and reduced across the group with shuffles.
+//  * The shared accumulator is flushed to global memory with atomics, since
+//    neighbouring tiles overlap in q layers of coefficients.
+#include <cuda_runtime.h>
+
+#include "sps_internal.h"
+
+namespace sps {
+
+namespace {
+
+__host__ __device__ constexpr int ipow4(int e) { return e <= 0 ? 1 : 4 * ipow4(e - 1); }
+
+// Values of the q+1 = 4 cubic B-splines that are nonzero on a cell, at local
+// coordinate t in [0, 1]: b[m] belongs to basis function (cell + m).  They are
+// the four polynomial pieces of the uniform cubic B-spline (de Boor 1978).
+template <typename T>
+__device__ __forceinline__ void cubic_basis(T t, T* b) {
+  const T omt = T(1) - t;
+  const T t2 = t * t;
+  b[0] = omt * omt * (omt * T(1.0 / 6.0));
+  b[1] = fma(t2, fma(t, T(0.5), T(-1.0)), T(2.0 / 3.0));
+  b[2] = fma(fma(fma(t, T(-0.5), T(0.5)), t, T(0.5)), t, T(1.0 / 6.0));
+  b[3] = t2 * (t * T(1.0 / 6.0));
+}
+
+template <int P, typename T, typename CT, int MODE>
+__global__ void __launch_bounds__(256, 1)
+k_point(const WorkItem* __restrict__ items, const int* __restrict__ run_begin,
+        const unsigned long long* __restrict__ run_cell, const CT* __restrict__ xs, long long n,
+        const double* __restrict__ ys, const T* __restrict__ v, T* __restrict__ u, LevelGeom geom) {
+  constexpr int R = P < 3 ? P : 3;            // dimensions held in a lane's registers
+  constexpr int NR = ipow4(R);
+  constexpr int F = P - R;                    // leading dimensions fixed per lane
+  constexpr int TPP = ipow4(F);               // lanes per run
+  constexpr bool VREG = sizeof(T) == 4;       // FP32: cache the cell's v in registers
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* acc = reinterpret_cast<T*>(smem_raw);
+  T* vp = acc + geom.patch;
+
+  const WorkItem it = items[blockIdx.x];
+  for (int e = threadIdx.x; e < geom.patch; e += blockDim.x) {
+    acc[e] = T(0);
+    if (MODE == PT_APPLY) {
+      int rem = e;
+      long long gi = 0;
+      bool inb = true;
+#pragma unroll
+      for (int p = P - 1; p >= 0; --p) {
+        const int m = rem % geom.E[p];
+        rem /= geom.E[p];
+        const int j = it.c0[p] + m;
+        inb = inb && j < geom.J[p];
+        gi += (long long)j * geom.stride[p];
+      }
+      vp[e] = inb ? v[gi] : T(0);
+    }
+  }
+  __syncthreads();
+
+  const int group = threadIdx.x / TPP;
+  const int glane = threadIdx.x % TPP;
+  const int ngroups = blockDim.x / TPP;
+  unsigned gmask = 0xffffffffu;
+  if (TPP < 32) gmask = ((1u << TPP) - 1u) << ((threadIdx.x & 31) & ~(TPP - 1));
+  int mfix[F > 0 ? F : 1];
+  {
+    int l = glane;
+#pragma unroll
+    for (int p = F - 1; p >= 0; --p) {
+      mfix[p] = l & 3;
+      l >>= 2;
+    }
+  }
+  T inv[P];
+#pragma unroll
+  for (int p = 0; p < P; ++p) inv[p] = T(geom.inv_h[p]);
+
+  for (int r = it.run_lo + group; r < it.run_hi; r += ngroups) {
+    const int i0 = run_begin[r], i1 = run_begin[r + 1];
+    const unsigned long long pc = run_cell[r];
+    T tsh[P];
+    int base = 0;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      const int c = (int)((pc >> (12 * p)) & 0xFFFull);
+      int o = c - it.c0[p];
+      if (p < F) o += mfix[p];
+      base += o * geom.Es[p];
+      tsh[p] = T(geom.lo[p] * geom.inv_h[p] + (double)c);   // t = x * inv - (lo * inv + c)
+    }
+    const int e0 = R >= 3 ? geom.Es[P - 3] : 0;
+    const int e1 = R >= 2 ? geom.Es[P - 2] : 0;
+    auto vidx = [&](int k) -> int {
+      if (R == 3) return base + (k >> 4) * e0 + ((k >> 2) & 3) * e1 + (k & 3);
+      if (R == 2) return base + (k >> 2) * e1 + (k & 3);
+      return base + k;
+    };
+    T vr[VREG ? NR : 1];
+    if (VREG && MODE == PT_APPLY) {
+#pragma unroll
+      for (int k = 0; k < NR; ++k) vr[VREG ? k : 0] = vp[vidx(k)];
+    }
+    T accr[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) accr[k] = T(0);
+
+    for (int i = i0; i < i1; ++i) {
+      T bv[P][4];
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        const T xp = T(xs[(long long)p * n + i]);
+        const T t = fma(xp, inv[p], -tsh[p]);
+        cubic_basis(t, bv[p]);
+        if (MODE == PT_DIAG) {
+#pragma unroll
+          for (int m = 0; m < 4; ++m) bv[p][m] *= bv[p][m];
+        }
+      }
+      T fixw = T(1);
+#pragma unroll
+      for (int p = 0; p < F; ++p) fixw *= bv[p][mfix[p]];
+      T s;
+      if (MODE == PT_APPLY) {
+        T g = T(0);
+        if (R == 3) {
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            T s2 = T(0);
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+              T s1 = T(0);
+#pragma unroll
+              for (int d = 0; d < 4; ++d) {
+                const int k = (a * 4 + b) * 4 + d;
+                const T vv = VREG ? vr[VREG ? k : 0] : vp[vidx(k)];
+                s1 = fma(bv[P - 1][d], vv, s1);
+              }
+              s2 = fma(bv[P - 2][b], s1, s2);
+            }
+            g = fma(bv[P - 3][a], s2, g);
+          }
+        } else if (R == 2) {
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            T s1 = T(0);
+#pragma unroll
+            for (int d = 0; d < 4; ++d) {
+              const int k = a * 4 + d;
+              const T vv = VREG ? vr[VREG ? k : 0] : vp[vidx(k)];
+              s1 = fma(bv[P - 1][d], vv, s1);
+            }
+            g = fma(bv[P - 2][a], s1, g);
+          }
+        } else {
+#pragma unroll
+          for (int d = 0; d < 4; ++d) {
+            const T vv = VREG ? vr[VREG ? d : 0] : vp[vidx(d)];
+            g = fma(bv[P - 1][d], vv, g);
+          }
+        }
+        g *= fixw;
+#pragma unroll
+        for (int o = TPP / 2; o >= 1; o >>= 1) g += __shfl_xor_sync(gmask, g, o, TPP);
+        s = g;
+      } else if (MODE == PT_RHS) {
+        s = T(ys[i]);
+      } else {
+        s = T(1);
+      }
+      const T w = s * fixw;
+      if (R == 3) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const T t1 = w * bv[P - 3][a];
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const T t2 = t1 * bv[P - 2][b];
+#pragma unroll
+            for (int d = 0; d < 4; ++d) accr[(a * 4 + b) * 4 + d] = fma(t2, bv[P - 1][d], accr[(a * 4 + b) * 4 + d]);
+          }
+        }
+      } else if (R == 2) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const T t1 = w * bv[P - 2][a];
+#pragma unroll
+          for (int d = 0; d < 4; ++d) accr[a * 4 + d] = fma(t1, bv[P - 1][d], accr[a * 4 + d]);
+        }
+      } else {
+#pragma unroll
+        for (int d = 0; d < 4; ++d) accr[d] = fma(w, bv[P - 1][d], accr[d]);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < NR; ++k) atomicAdd(&acc[vidx(k)], accr[k]);
+  }
+  __syncthreads();
+
+  for (int e = threadIdx.x; e < geom.patch; e += blockDim.x) {
+    const T a = acc[e];
+    if (a == T(0)) continue;
+    int rem = e;
+    long long gi = 0;
+    bool inb = true;
+#pragma unroll
+    for (int p = P - 1; p >= 0; --p) {
+      const int m = rem % geom.E[p];
+      rem /= geom.E[p];
+      const int j = it.c0[p] + m;
+      inb = inb && j < geom.J[p];
+      gi += (long long)j * geom.stride[p];
+    }
+    if (inb) atomicAdd(&u[gi], a);
+  }
+}
+
+// Event pool for sps_profile_begin / sps_profile_end.
+struct ProfileState {
+  bool active = false;
+  int used = 0;
+  std::vector<cudaEvent_t> ev;   // pairs
+};
+ProfileState g_prof;
+constexpr int PROFILE_MAX = 8192;
+
+template <int P, typename T, typename CT, int MODE>
+int launch_point(sps_plan* pl, const Level& L, const T* v, T* u, cudaStream_t st) {
+  if (L.nitems == 0) return SPS_OK;
+  const size_t smem = (size_t)(MODE == PT_APPLY ? 2 : 1) * L.geom.patch * sizeof(T);
+  static bool attr_set = false;
+  if (!attr_set) {
+    SPS_CUDA(cudaFuncSetAttribute(k_point<P, T, CT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  160 * 1024));
+    attr_set = true;
+  }
+  const bool timed = MODE == PT_APPLY && g_prof.active && g_prof.used < PROFILE_MAX;
+  if (timed) SPS_CUDA(cudaEventRecord(g_prof.ev[2 * g_prof.used], st));
+  k_point<P, T, CT, MODE><<<L.nitems, 256, smem, st>>>(L.items, L.run_begin, L.run_cell,
+                                                       (const CT*)pl->x_sorted, pl->n, pl->y_sorted, v, u,
+                                                       L.geom);
+  SPS_CHECK_LAUNCH("point operator");
+  if (timed) SPS_CUDA(cudaEventRecord(g_prof.ev[2 * g_prof.used++ + 1], st));
+  return SPS_OK;
+}
+
+template <int P, typename T>
+int dispatch_mode(sps_plan* pl, const Level& L, int mode, const T* v, T* u, cudaStream_t st) {
+  if (pl->dtype == SPS_F64) {
+    if (mode == PT_APPLY) return launch_point<P, T, double, PT_APPLY>(pl, L, v, u, st);
+    if (mode == PT_DIAG) return launch_point<P, T, double, PT_DIAG>(pl, L, v, u, st);
+    return launch_point<P, T, double, PT_RHS>(pl, L, v, u, st);
+  }
+  if (mode == PT_APPLY) return launch_point<P, T, float, PT_APPLY>(pl, L, v, u, st);
+  if (mode == PT_DIAG) return launch_point<P, T, float, PT_DIAG>(pl, L, v, u, st);
+  return launch_point<P, T, float, PT_RHS>(pl, L, v, u, st);
+}
+
+}  // namespace
+
+template <typename T>
+int point_op(sps_plan* pl, int g, int mode, const T* v, T* u, cudaStream_t st) {
+  const Level& L = pl->lev[g - 1];
+  switch (pl->P) {
+    case 1: return dispatch_mode<1, T>(pl, L, mode, v, u, st);
+    case 2: return dispatch_mode<2, T>(pl, L, mode, v, u, st);
+    case 3: return dispatch_mode<3, T>(pl, L, mode, v, u, st);
+    case 4: return dispatch_mode<4, T>(pl, L, mode, v, u, st);
+    case 5: return dispatch_mode<5, T>(pl, L, mode, v, u, st);
+  }
+  set_error("unsupported dimension");
+  return SPS_EINVAL;
+}
+
+template int point_op<double>(sps_plan*, int, int, const double*, double*, cudaStream_t);
+template int point_op<float>(sps_plan*, int, int, const float*, float*, cudaStream_t);
+
+int profile_begin() {
+  if (g_prof.ev.empty()) {
+    g_prof.ev.resize(2 * PROFILE_MAX);
+    for (auto& e : g_prof.ev) SPS_CUDA(cudaEventCreate(&e));
+  }
+  g_prof.used = 0;
+  g_prof.active = true;
+  return SPS_OK;
+}
+
+int profile_end(double* ms, unsigned long long* launches) {
+  g_prof.active = false;
+  double tot = 0.0;
+  for (int i = 0; i < g_prof.used; ++i) {
+    SPS_CUDA(cudaEventSynchronize(g_prof.ev[2 * i + 1]));
+    float t = 0.0f;
+    SPS_CUDA(cudaEventElapsedTime(&t, g_prof.ev[2 * i], g_prof.ev[2 * i + 1]));
+    tot += t;
+  }
+  *ms = tot;
+  *launches = (unsigned long long)g_prof.used;
+  return SPS_OK;
+}
+
+}  // namespace sps

@@ -1,0 +1,189 @@
+// Internal declarations of the spline smoothing library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sps.h"
+
+namespace sps {
+
+constexpr int Q = 3;                 // cubic B-splines
+constexpr int BAND = 2 * Q + 1;      // diagonals of the 1-D Gram matrices
+constexpr int MAXP = SPS_MAX_DIM;
+constexpr int MAXL = SPS_MAX_LEVELS;
+constexpr int RUN_MAX = 32;          // points per run (one thread group, one cell)
+constexpr int COARSE_MAX = 4096;     // K_1 limit of the dense coarse inverse
+
+// Geometry of one grid level, passed by value to kernels.
+struct LevelGeom {
+  int P;
+  int N[MAXP];          // knot intervals per dimension
+  int J[MAXP];          // N + q coefficients per dimension
+  long long stride[MAXP];
+  long long K;
+  int shift;            // level cell = finest cell >> shift
+  double inv_h[MAXP];   // N_p / (hi_p - lo_p) at this level
+  double lo[MAXP];
+  int ts;               // tile side in level cells (power of two)
+  int E[MAXP];          // patch extent per dimension: min(ts, N_p) + q
+  int Es[MAXP];         // patch strides (last dimension fastest)
+  int patch;            // prod E
+};
+
+// One CTA of the point operator: runs [run_lo, run_hi) of one tile.
+struct WorkItem {
+  int run_lo, run_hi;
+  int c0[MAXP];         // tile origin in level cells
+  int pad[8 - 2 - MAXP > 0 ? 8 - 2 - MAXP : 1];
+};
+
+template <typename T>
+struct LevelVecs {
+  T* alpha = nullptr;   // smoother iterate / correction on this level
+  T* b = nullptr;       // right-hand side on this level
+  T* u = nullptr;       // operator output
+  T* dinv = nullptr;    // 1 / diag(A_g)
+  T* band = nullptr;    // Gram bands [p][r][J_p][BAND]
+};
+
+struct Level {
+  LevelGeom geom;
+  // runs: points [run_begin[r], run_begin[r+1]) share one level cell run_cell[r]
+  int* run_begin = nullptr;
+  unsigned long long* run_cell = nullptr;   // 12 bits per dimension
+  int nruns = 0;
+  WorkItem* items = nullptr;
+  int nitems = 0;
+  double omega = 0.0;
+  double* diag = nullptr;                   // FP64 diag(A_g)
+  LevelVecs<double> d;
+  LevelVecs<float> f;
+};
+
+}  // namespace sps
+
+struct sps_plan {
+  int P = 0, q = 3, G = 0;
+  double lam = 0.0;
+  int N[sps::MAXP] = {0};
+  double lo[sps::MAXP] = {0}, hi[sps::MAXP] = {0};
+  sps_options opt;
+  int device = 0;
+  int Lbits = 1;            // bits per dimension of the Morton key
+  sps::Level lev[sps::MAXL];
+  // points (sorted)
+  long long n = 0, n_cap = 0;
+  int dtype = SPS_F64;
+  void* x_sorted = nullptr;   // P x n SoA in the input dtype
+  double* y_sorted = nullptr;
+  unsigned long long* keys = nullptr;
+  unsigned int* perm = nullptr;
+  // scratch for the sort (n entries each) and segment building
+  unsigned long long* keys_tmp = nullptr;
+  unsigned int* perm_tmp = nullptr;
+  unsigned int* sort_hist = nullptr;
+  long long sort_hist_cap = 0;
+  int* seg_tmp = nullptr;       // per-segment counts / offsets
+  long long seg_cap = 0;
+  int* err_flag = nullptr;      // device error flag
+  // right-hand side Phi'y (FP64) and its norm
+  double* rhs = nullptr;
+  double rhs_norm = 0.0;
+  // coarse inverse (FP64 and FP32 copies)
+  double* coarse_inv = nullptr;
+  float* coarse_inv_f = nullptr;
+  double* coarse_tmp = nullptr;   // row/column snapshots for the inversion
+  // penalty and transfer temporaries (max K over levels)
+  double* dtmp[8] = {nullptr};
+  float* ftmp[8] = {nullptr};
+  // outer PCG vectors (FP64, K_G)
+  double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *v = nullptr, *rprev = nullptr;
+  float* p32 = nullptr;
+  double* scal = nullptr;         // device scalars
+  double* red_part = nullptr;     // reduction partials
+  unsigned int* red_count = nullptr;
+  double* host_scal = nullptr;    // pinned mirror of scal
+  bool have_points = false;
+};
+
+namespace sps {
+
+// ---- error handling ----
+void set_error(const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+#define SPS_CUDA(call)                                   \
+  do {                                                   \
+    cudaError_t _e = (call);                             \
+    if (_e != cudaSuccess) return sps::cuda_fail(_e, #call); \
+  } while (0)
+// every kernel launch is followed by this check, which also counts the launch
+void count_launches(unsigned long long k);
+#define SPS_CHECK_LAUNCH(what)  \
+  do {                          \
+    sps::count_launches(1);     \
+    SPS_CUDA(cudaGetLastError()); \
+  } while (0)
+
+// ---- sort.cu ----
+int compute_keys(sps_plan* pl, const void* x_dev, int dtype, cudaStream_t st);
+int radix_sort(sps_plan* pl, int nbits, cudaStream_t st);
+int gather_points(sps_plan* pl, const void* x_dev, const void* y_dev, int dtype, cudaStream_t st);
+int build_level_work(sps_plan* pl, int g, cudaStream_t st);
+
+// ---- point_op.cu ----
+enum PointMode { PT_APPLY = 0, PT_DIAG = 1, PT_RHS = 2 };
+template <typename T>
+int point_op(sps_plan* pl, int g, int mode, const T* v, T* u, cudaStream_t st);
+int profile_begin();
+int profile_end(double* ms, unsigned long long* launches);
+
+// ---- grid_ops.cu ----
+template <typename T>
+int penalty_apply(sps_plan* pl, int g, const T* v, T* out, double scale, cudaStream_t st);
+int penalty_diag(sps_plan* pl, int g, double* d, cudaStream_t st);
+template <typename T>
+int prolong_sub(sps_plan* pl, int g, const T* c, T* f, int mode, cudaStream_t st);  // mode 0: f = Ic; 1: f -= Ic
+template <typename T>
+int restrict_res(sps_plan* pl, int g, const T* f, const T* fb, T* c, cudaStream_t st);  // c = I'(f - fb) (fb may be null)
+int coarse_assemble(sps_plan* pl, cudaStream_t st);
+template <typename T>
+int coarse_solve(sps_plan* pl, const T* r, T* e, cudaStream_t st);
+
+// elementwise / reductions
+template <typename T>
+int vec_scale_mul(T* out, const T* a, const T* b, T s, long long n, cudaStream_t st);     // out = s*a*b
+template <typename T>
+int vec_jacobi(T* alpha, const T* dinv, const T* b, const T* u, T omega, long long n, cudaStream_t st);
+int vec_cast_d2f(float* out, const double* in, long long n, cudaStream_t st);
+int vec_cast_f2d(double* out, const float* in, long long n, cudaStream_t st);
+int vec_set_d(double* out, double v, long long n, cudaStream_t st);
+int vec_set_f(float* out, float v, long long n, cudaStream_t st);
+int vec_recip(double* dinv, float* dinv_f, const double* d, long long n, cudaStream_t st);
+int vec_residual(double* r, const double* b, const double* u, long long n, double* scal, int slot,
+                 sps_plan* pl, cudaStream_t st);  // r = b - u; scal[slot] = r.r
+int dot(sps_plan* pl, const double* a, const double* b, long long n, int slot, cudaStream_t st);
+int dot2(sps_plan* pl, const double* a, const double* b, const double* c, long long n, int slot,
+         cudaStream_t st);   // scal[slot] = a.b, scal[slot+1] = a.c
+int pcg_update_xr(sps_plan* pl, long long n, int rz_slot, cudaStream_t st);
+int pcg_update_p(sps_plan* pl, long long n, int num_slot, int den_slot, int flexible, cudaStream_t st);
+
+// ---- solver (api.cu) ----
+template <typename T>
+int apply_level(sps_plan* pl, int g, const T* v, T* u, cudaStream_t st);
+template <typename T>
+int vcycle_into(sps_plan* pl, const T* bG, T* xG, cudaStream_t st);   // xG = V(bG) on level G
+
+template <typename T>
+LevelVecs<T>& vecs(Level& L);
+template <>
+inline LevelVecs<double>& vecs<double>(Level& L) { return L.d; }
+template <>
+inline LevelVecs<float>& vecs<float>(Level& L) { return L.f; }
+
+int grid_blocks(long long n, int threads);
+
+}  // namespace sps

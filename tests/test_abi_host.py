@@ -1,0 +1,96 @@
+"""The C ABI on the host: the library builds, loads without a GPU, exports
+every function include/sps.h declares, and rejects bad arguments before any
+device work."""
+import ctypes as C
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+from paper_1901_00654_gb300 import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "sps.h")
+
+
+@pytest.fixture(scope="module")
+def B():
+    build.build_library()
+    from paper_1901_00654_gb300 import binding
+    return binding
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"SPS_API\s+[\w\s\*]+?\b(sps_\w+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(B):
+    names = declared_functions()
+    assert len(names) >= 20
+    lib = C.CDLL(build.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(B.EXPORTED) == names
+
+
+def test_struct_layouts_match_header(B):
+    """sizeof/offsetof of the ABI structs from a C compiler equal the ctypes view."""
+    src = r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "sps.h"
+int main(void) {
+  printf("%zu %zu %zu %zu\n", sizeof(sps_options), offsetof(sps_options, replace_ratio),
+         sizeof(sps_result), offsetof(sps_result, solve_ms));
+  return 0;
+}
+'''
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        exe = os.path.join(d, "t")
+        open(c, "w").write(src)
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        vals = [int(v) for v in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
+    assert vals == [C.sizeof(B.sps_options), B.sps_options.replace_ratio.offset,
+                    C.sizeof(B.sps_result), B.sps_result.solve_ms.offset]
+
+
+def test_defaults(B):
+    o = B.sps_default_options()
+    assert (o.precision, o.nu1, o.nu2, o.omega, o.max_iter) == (B.SPS_PREC_FP64, 1, 1, 0.0, 500)
+
+
+@pytest.mark.parametrize("args", [
+    dict(P=0, intervals=[8]),
+    dict(P=6, intervals=[8] * 6),
+    dict(P=2, intervals=[8, 12]),
+    dict(P=2, intervals=[8, 8], q=2),
+    dict(P=2, intervals=[8, 8], levels=5),
+    dict(P=2, intervals=[8, 8], lam=-1.0),
+    dict(P=2, intervals=[8, 8], lam=float("nan")),
+    dict(P=3, intervals=[1024, 1024, 1024]),
+    dict(P=2, intervals=[8, 8], lo=[0.0, 1.0], hi=[1.0, 1.0]),
+    dict(P=5, intervals=[16] * 5, levels=1),
+])
+def test_plan_create_rejects_bad_arguments(B, args):
+    a = dict(q=3, levels=2, lam=1e-3, lo=None, hi=None)
+    a.update(args)
+    P = a["P"]
+    h = C.c_void_p()
+    iv = (C.c_int * max(P, 1))(*a["intervals"][:max(P, 1)])
+    lo = (C.c_double * P)(*a["lo"]) if a["lo"] else None
+    hi = (C.c_double * P)(*a["hi"]) if a["hi"] else None
+    code = B.lib().sps_plan_create(C.byref(h), P, a["q"], iv, lo, hi, a["levels"], a["lam"], None)
+    assert code == B.SPS_EINVAL
+    assert h.value is None
+    assert len(B.sps_last_error()) > 0
+
+
+def test_null_handles(B):
+    assert B.lib().sps_destroy(None) == B.SPS_OK
+    assert B.lib().sps_solve(None, None, 0, 1e-8, None, None) == B.SPS_EINVAL
+    assert B.lib().sps_set_points(None, 10, None, None, 1, 0, None) == B.SPS_EINVAL
+    assert B.lib().sps_launch_count(None) == B.SPS_EINVAL

@@ -1,0 +1,272 @@
+"""Parity of every CUDA step with the CPU oracle, called through the C ABI.
+
+Tolerances: FP64 kernels agree with the oracle to 1e-12 relative (max norm)
+per operator application (different summation order only); FP32 kernels of
+the mixed mode to 2e-5; integer work (cell index, key, permutation) exactly.
+The solve is compared at tol = 1e-13 with a 1e-8 relative coefficient bound
+(the stated FP64 target).
+"""
+import numpy as np
+import pytest
+
+from oracle import mgcg, spline
+from tests.gpu_util import level_ops, oracle_hierarchy, random_problem, rel_err
+
+pytestmark = pytest.mark.gpu
+
+B = pytest.importorskip("paper_1901_00654_gb300.binding")
+
+FP64_TOL = 1e-12
+FP32_TOL = 2e-5
+
+# (P, intervals, levels, n): several tiles per level, ragged run/item tails
+CASES = [
+    (1, [64], 4, 3001),
+    (2, [16, 32], 3, 5003),
+    (3, [8, 16, 8], 3, 6007),
+    (4, [4, 8, 4, 4], 2, 4001),
+    (5, [2, 2, 4, 2, 2], 2, 2003),
+]
+
+
+@pytest.fixture(scope="module", params=CASES, ids=lambda c: "P%d" % c[0])
+def case(request):
+    P, intervals, G, n = request.param
+    x, y, lo, hi = random_problem(P, intervals, n, seed=100 + P)
+    lam = 3e-3
+    plan = B.Plan(P, intervals, G, lam, lo, hi)
+    plan.set_points(x, y)
+    ops = level_ops(x, y, lo, hi, intervals, 3, lam, G)
+    yield dict(P=P, intervals=intervals, G=G, n=n, x=x, y=y, lo=lo, hi=hi, lam=lam, plan=plan, ops=ops)
+    plan.close()
+
+
+def test_sort_bit_exact(case):
+    perm_o, key_o, _ = spline.sort_permutation(case["x"], case["lo"], case["hi"], case["intervals"])
+    perm = np.zeros(case["n"], dtype=np.int64)
+    key = np.zeros(case["n"], dtype=np.uint64)
+    B.sps_get_sort(case["plan"].h, perm, key)
+    np.testing.assert_array_equal(perm, perm_o)
+    np.testing.assert_array_equal(key, key_o[perm_o])
+
+
+def test_rhs(case):
+    b = np.zeros(case["plan"].K)
+    B.sps_rhs(case["plan"].h, b)
+    assert rel_err(b, case["ops"][case["G"]]["b"]) < FP64_TOL
+
+
+@pytest.mark.parametrize("prec", [B.SPS_PREC_FP64, B.SPS_PREC_MIXED])
+def test_apply_every_level(case, prec):
+    r = np.random.default_rng(1)
+    tol = FP64_TOL if prec == B.SPS_PREC_FP64 else FP32_TOL
+    for g in range(1, case["G"] + 1):
+        A = case["ops"][g]["A"]
+        v = r.standard_normal(A.shape[0])
+        u = np.zeros_like(v)
+        B.sps_apply(case["plan"].h, g, prec, v, u)
+        assert rel_err(u, A @ v) < tol, (g, rel_err(u, A @ v))
+
+
+@pytest.mark.parametrize("prec", [B.SPS_PREC_FP64, B.SPS_PREC_MIXED])
+def test_point_operator_every_level(case, prec):
+    """Phi_g'(Phi_g v) alone (Algorithms 3 and 4) against the explicit sparse Phi_g."""
+    r = np.random.default_rng(7)
+    tol = FP64_TOL if prec == B.SPS_PREC_FP64 else FP32_TOL
+    for g in range(1, case["G"] + 1):
+        Phi = spline.phi_matrix(case["x"], case["lo"], case["hi"], case["ops"][g]["N"], 3)
+        v = r.standard_normal(Phi.shape[1])
+        u = np.zeros_like(v)
+        B.sps_point_apply(case["plan"].h, g, prec, v, u)
+        assert rel_err(u, Phi.T @ (Phi @ v)) < tol
+
+
+@pytest.mark.parametrize("prec", [B.SPS_PREC_FP64, B.SPS_PREC_MIXED])
+def test_penalty_every_level(case, prec):
+    r = np.random.default_rng(2)
+    tol = FP64_TOL if prec == B.SPS_PREC_FP64 else FP32_TOL
+    for g in range(1, case["G"] + 1):
+        L = case["ops"][g]["Lam"]
+        v = r.standard_normal(L.shape[0])
+        u = np.zeros_like(v)
+        B.sps_penalty_apply(case["plan"].h, g, prec, v, u)
+        assert rel_err(u, L @ v) < tol * 10
+
+
+def test_diag_every_level(case):
+    for g in range(1, case["G"] + 1):
+        d = np.zeros(case["ops"][g]["A"].shape[0])
+        B.sps_diag(case["plan"].h, g, d)
+        assert rel_err(d, case["ops"][g]["A"].diagonal()) < FP64_TOL
+
+
+@pytest.mark.parametrize("prec", [B.SPS_PREC_FP64, B.SPS_PREC_MIXED])
+def test_transfers(case, prec):
+    r = np.random.default_rng(3)
+    tol = FP64_TOL if prec == B.SPS_PREC_FP64 else FP32_TOL
+    for g in range(2, case["G"] + 1):
+        I = case["ops"][g]["I"]
+        c = r.standard_normal(I.shape[1])
+        f = np.zeros(I.shape[0])
+        B.sps_prolong(case["plan"].h, g, prec, c, f)
+        assert rel_err(f, I @ c) < tol
+        fv = r.standard_normal(I.shape[0])
+        cv = np.zeros(I.shape[1])
+        B.sps_restrict(case["plan"].h, g, prec, fv, cv)
+        assert rel_err(cv, I.T @ fv) < tol
+
+
+def test_coarse_solve(case):
+    A1 = case["ops"][1]["A"].toarray()
+    r = np.random.default_rng(4).standard_normal(A1.shape[0])
+    e = np.zeros_like(r)
+    B.sps_coarse_solve(case["plan"].h, r, e)
+    ref = np.linalg.solve(A1, r)
+    # the explicit inverse costs a factor kappa(A_1) in accuracy
+    assert rel_err(e, ref) < 1e-14 * np.linalg.cond(A1) + 1e-12
+
+
+def test_vcycle_matches_oracle(case):
+    G = case["G"]
+    om = B.sps_get_omega(case["plan"].h, G)
+    H = oracle_hierarchy(case["x"], case["y"], case["lo"], case["hi"], case["intervals"], 3, case["lam"], G, om)
+    r = np.random.default_rng(5).standard_normal(H.levels[-1].A.shape[0])
+    z = np.zeros_like(r)
+    B.sps_vcycle(case["plan"].h, B.SPS_PREC_FP64, r, z)
+    ref = mgcg.v_cycle(H, G, r, 1, 1)
+    A1 = case["ops"][1]["A"].toarray()
+    assert rel_err(z, ref) < 1e-14 * np.linalg.cond(A1) + 1e-11
+    z32 = np.zeros_like(r)
+    B.sps_vcycle(case["plan"].h, B.SPS_PREC_MIXED, r, z32)
+    assert rel_err(z32, ref) < 1e-3
+
+
+def test_omega_is_safe_damping(case):
+    """omega_g = 4 / (3 lambda_max(D^-1 A)) from the power iteration: the
+    smoother stays convergent (omega lambda_max < 2) and near 4/3."""
+    om = B.sps_get_omega(case["plan"].h, case["G"])
+    for g in range(2, case["G"] + 1):
+        A = case["ops"][g]["A"]
+        lmax = mgcg.lambda_max_jacobi(A, 1.0 / A.diagonal())
+        assert 4.0 / 3.0 - 1e-3 <= om[g - 1] * lmax < 1.9
+
+
+def test_solve_matches_direct(case):
+    plan = case["plan"]
+    coef, res = plan.solve(1e-13)
+    A, b = case["ops"][case["G"]]["A"], case["ops"][case["G"]]["b"]
+    ref = mgcg.solve_direct(A, b)
+    assert res.status == B.SPS_OK and res.rel_res_true <= 1e-13
+    assert rel_err(coef, ref) < 1e-8
+
+
+def test_mixed_solve_matches_direct(case):
+    P, intervals, G = case["P"], case["intervals"], case["G"]
+    with B.Plan(P, intervals, G, case["lam"], case["lo"], case["hi"], precision=B.SPS_PREC_MIXED) as pl:
+        pl.set_points(case["x"], case["y"])
+        coef, res = pl.solve(1e-12)
+        assert res.status == B.SPS_OK and res.rel_res_true <= 1e-12
+        ref = mgcg.solve_direct(case["ops"][G]["A"], case["ops"][G]["b"])
+        assert rel_err(coef, ref) < 1e-7
+
+
+# ------------------------------------------------------------------ the PR1 workload
+
+def test_pr1_iterations_and_coefficients():
+    import workloads as W
+    pr = W.pr1()
+    with B.Plan(pr.P, pr.intervals, pr.levels, pr.lam, pr.lo, pr.hi) as pl:
+        pl.set_points(pr.x, pr.y)
+        om = B.sps_get_omega(pl.h, pr.levels)
+        coef, res = pl.solve(pr.tol)
+        H = oracle_hierarchy(pr.x, pr.y, pr.lo, pr.hi, pr.intervals, 3, pr.lam, pr.levels, om)
+        ores = mgcg.mgcg(H, pr.tol)
+        assert abs(res.iterations - ores.iterations) <= 1
+        assert res.rel_res_true <= pr.tol
+        coef2, _ = pl.solve(1e-13)
+        ref = mgcg.solve_direct(H.levels[-1].A, H.b)
+        assert rel_err(coef2, ref) < 1e-8
+
+
+# ------------------------------------------------------------------ edge cases
+
+def test_float32_inputs_and_device_buffers():
+    torch = pytest.importorskip("torch")
+    x, y, lo, hi = random_problem(3, [8, 8, 8], 4000, seed=9, dtype=np.float32)
+    with B.Plan(3, [8, 8, 8], 3, 1e-2) as pl:
+        pl.set_points(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda())
+        perm = np.zeros(4000, dtype=np.int64)
+        B.sps_get_sort(pl.h, perm)
+        np.testing.assert_array_equal(perm, spline.sort_permutation(x, lo, hi, [8, 8, 8])[0])
+        coef = torch.zeros(pl.K, dtype=torch.float64, device="cuda")
+        _, res = pl.solve(1e-12, coef)
+        A, b, _, _ = spline.system(x, y, lo, hi, [8, 8, 8], 3, 1e-2)
+        assert rel_err(coef.cpu().numpy(), mgcg.solve_direct(A, b)) < 1e-8
+
+
+def test_errors_are_reported():
+    with B.Plan(2, [8, 8], 2, 1e-3) as pl:
+        x = np.array([[0.5, 0.5], [1.5, 0.2]])
+        with pytest.raises(B.SpsError) as e:
+            pl.set_points(x, np.zeros(2))
+        assert e.value.code == B.SPS_EDOM
+        x = np.array([[0.5, np.nan]])
+        with pytest.raises(B.SpsError) as e:
+            pl.set_points(x, np.zeros(1))
+        assert e.value.code == B.SPS_EDOM
+        with pytest.raises(B.SpsError) as e:
+            pl.set_points(np.zeros((0, 2)), np.zeros(0))
+        assert e.value.code == B.SPS_EEMPTY
+        with pytest.raises(B.SpsError) as e:
+            pl.solve(1e-8)
+        assert e.value.code == B.SPS_ESTATE
+    with pytest.raises(B.SpsError) as e:
+        B.Plan(2, [12, 8], 2, 1e-3)
+    assert e.value.code == B.SPS_EINVAL
+    with pytest.raises(B.SpsError) as e:
+        B.Plan(2, [8, 8], 5, 1e-3)
+    assert e.value.code == B.SPS_EINVAL
+
+
+def test_single_level_and_single_cell():
+    """G = 1 is the exact coarse solve; all points in one cell and on its faces."""
+    x = np.array([[0.0, 0.0], [1.0, 1.0], [0.0, 1.0], [1.0, 0.0], [0.5, 0.5], [0.25, 0.75]] * 10)
+    y = np.arange(x.shape[0], dtype=np.float64) % 3
+    with B.Plan(2, [1, 1], 1, 1e-2) as pl:
+        pl.set_points(x, y)
+        coef, res = pl.solve(1e-12)
+        A, b, _, _ = spline.system(x, y, [0, 0], [1, 1], [1, 1], 3, 1e-2)
+        assert rel_err(coef, np.linalg.solve(A.toarray(), b)) < 1e-9
+
+
+def test_zero_response_gives_zero():
+    x, _, lo, hi = random_problem(2, [8, 8], 500, seed=3)
+    with B.Plan(2, [8, 8], 3, 1e-2) as pl:
+        pl.set_points(x, np.zeros(500))
+        coef, res = pl.solve(1e-10)
+        assert np.all(coef == 0.0)
+
+
+def test_warm_start_converges_immediately():
+    x, y, lo, hi = random_problem(2, [16, 16], 3000, seed=4)
+    with B.Plan(2, [16, 16], 3, 1e-3, warm_start=1) as pl:
+        pl.set_points(x, y)
+        c0 = np.zeros(pl.K)
+        c0, r0 = pl.solve(1e-12, c0)
+        c1 = c0.copy()
+        c1, r1 = pl.solve(1e-10, c1)
+        assert r1.iterations == 0 and rel_err(c1, c0) < 1e-12
+
+
+def test_null_space_recovery_gpu():
+    """Affine data: the GPU solution is the affine Greville tensor for any lambda."""
+    P, intervals = 3, [8, 8, 16]
+    x, _, lo, hi = random_problem(P, intervals, 20000, seed=6)
+    c = np.array([0.3, -1.0, 2.0, 0.5])
+    y = c[0] + x @ c[1:]
+    with B.Plan(P, intervals, 3, 10.0) as pl:
+        pl.set_points(x, y)
+        coef, res = pl.solve(1e-13)
+    grids = np.meshgrid(*[spline.greville(lo[p], hi[p], intervals[p], 3) for p in range(P)], indexing="ij")
+    ref = c[0] + sum(c[p + 1] * grids[p] for p in range(P))
+    assert rel_err(coef, ref.ravel()) < 1e-9
