@@ -80,7 +80,7 @@ typedef struct sps_options {
     double omega;          /* Jacobi damping; <= 0 (default): per level
                               4 / (3 lambda_max(D_g^-1 A_g)) by power iteration */
     int    power_iters;    /* power iterations for omega (default 20) */
-    int    max_iter;       /* outer iteration cap (default 500) */
+    int    max_iter;       /* outer iteration cap (default 20000) */
     int    warm_start;     /* 1: coef passed to sps_solve is the initial guess */
     int    tile;           /* tile side in cells, 0 = automatic per P */
     double replace_ratio;  /* MIXED: recompute the FP64 residual when |r| has

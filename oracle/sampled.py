@@ -125,3 +125,29 @@ def rhs_chunked(x, y, lo, hi, intervals, q, chunk: int = 20000) -> np.ndarray:
         cols, vals = _point_rows(x[s:s + chunk], lo, hi, intervals, q)
         b += np.bincount(cols.ravel(), weights=(vals * y[s:s + chunk, None]).ravel(), minlength=K)
     return b
+
+
+def penalty_apply_kron(v, lo, hi, intervals, q) -> np.ndarray:
+    """Lambda v = sum_{|r|=2} (2/r!) (kron_p Psi^p_{r_p}) v without forming
+    Lambda: v is reshaped to the J_1 x ... x J_P tensor (last index fastest)
+    and each 1-D Gram matrix is applied along its own axis, the Kronecker
+    matrix-vector product of Algorithm 2."""
+    P = len(intervals)
+    J = [N + q for N in intervals]
+    grams = [[spline.gram_1d(lo[p], hi[p], intervals[p], q, r) for r in range(3)] for p in range(P)]
+    V = np.asarray(v, dtype=np.float64).reshape(J)
+    out = np.zeros_like(V)
+    for r, w in spline.penalty_multiindices(P):
+        T = V
+        for p in range(P):
+            T = np.moveaxis(np.tensordot(grams[p][r[p]], T, axes=([1], [p])), 0, p)
+        out += w * T
+    return out.ravel()
+
+
+def residual_norm(x, y, alpha, lo, hi, intervals, q, lam, chunk: int = 20000) -> float:
+    """|Phi'y - (Phi'Phi + lambda Lambda) alpha|_2 / |Phi'y|_2, matrix free."""
+    b = rhs_chunked(x, y, lo, hi, intervals, q, chunk)
+    Av = apply_phitphi_chunked(x, alpha, lo, hi, intervals, q, chunk) + lam * penalty_apply_kron(alpha, lo, hi,
+                                                                                                intervals, q)
+    return float(np.linalg.norm(b - Av) / np.linalg.norm(b))

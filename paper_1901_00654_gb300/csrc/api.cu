@@ -502,7 +502,7 @@ void sps_default_options(sps_options* opt) {
   opt->nu2 = 1;
   opt->omega = 0.0;
   opt->power_iters = 20;
-  opt->max_iter = 500;
+  opt->max_iter = 20000;
   opt->warm_start = 0;
   opt->tile = 0;
   opt->replace_ratio = 1e-2;

@@ -60,7 +60,7 @@ int main(void) {
 
 def test_defaults(B):
     o = B.sps_default_options()
-    assert (o.precision, o.nu1, o.nu2, o.omega, o.max_iter) == (B.SPS_PREC_FP64, 1, 1, 0.0, 500)
+    assert (o.precision, o.nu1, o.nu2, o.omega, o.max_iter) == (B.SPS_PREC_FP64, 1, 1, 0.0, 20000)
 
 
 @pytest.mark.parametrize("args", [

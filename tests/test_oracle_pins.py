@@ -422,6 +422,10 @@ def test_sampled_and_chunked_apply_match_assembled():
     np.testing.assert_allclose(sampled.apply_phitphi_chunked(x, v, lo, hi, intervals, q, chunk=700),
                                Phi.T @ (Phi @ v), rtol=1e-12, atol=1e-12 * np.abs(A @ v).max())
     np.testing.assert_allclose(sampled.rhs_chunked(x, y, lo, hi, intervals, q, chunk=700), b, atol=1e-11)
+    np.testing.assert_allclose(sampled.penalty_apply_kron(v, lo, hi, intervals, q), Lam @ v,
+                               atol=1e-12 * np.abs(Lam @ v).max())
+    alpha = mgcg.solve_direct(A, b)
+    assert sampled.residual_norm(x, y, alpha, lo, hi, intervals, q, lam, chunk=900) < 1e-11
 
 
 # ------------------------------------------------------------------ planted mistakes
