@@ -12,6 +12,8 @@
 //    contiguous "run" (at most RUN_MAX points).  A CTA owns the runs of one
 //    tile of ts^P cells; the (ts+q)^P coefficients its points can touch are
 //    staged in shared memory.
+//  * The item's point coordinates are contiguous after the sort and are
+//    staged in shared memory with coalesced loads before the run loop.
 //  * A group of TPP = 4^(P-3) lanes (1 lane for P <= 3) takes one run at a
 //    time.  Each lane owns 64 (or 4^P) of the cell's (q+1)^P coefficients and
 //    keeps their partial sums in registers while it walks the run, so the
@@ -44,7 +46,7 @@ __device__ __forceinline__ void cubic_basis(T t, T* b) {
 }
 
 template <int P, typename T, typename CT, int MODE>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(POINT_THREADS, 2)
 k_point(const WorkItem* __restrict__ items, const int* __restrict__ run_begin,
         const unsigned long long* __restrict__ run_cell, const CT* __restrict__ xs, long long n,
         const double* __restrict__ ys, const T* __restrict__ v, T* __restrict__ u, LevelGeom geom) {
@@ -56,8 +58,16 @@ k_point(const WorkItem* __restrict__ items, const int* __restrict__ run_begin,
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* acc = reinterpret_cast<T*>(smem_raw);
   T* vp = acc + geom.patch;
+  // the item's points (contiguous after the sort) are staged here, one array per dimension
+  const size_t xoff = ((size_t)(MODE == PT_APPLY ? 2 : 1) * geom.patch * sizeof(T) + 15) & ~(size_t)15;
+  CT* xsh = reinterpret_cast<CT*>(smem_raw + xoff);
 
   const WorkItem it = items[blockIdx.x];
+  const int pbeg = run_begin[it.run_lo];
+  const int npts = run_begin[it.run_hi] - pbeg;
+#pragma unroll
+  for (int p = 0; p < P; ++p)
+    for (int e = threadIdx.x; e < npts; e += blockDim.x) xsh[p * npts + e] = xs[(long long)p * n + pbeg + e];
   for (int e = threadIdx.x; e < geom.patch; e += blockDim.x) {
     acc[e] = T(0);
     if (MODE == PT_APPLY) {
@@ -128,7 +138,7 @@ k_point(const WorkItem* __restrict__ items, const int* __restrict__ run_begin,
       T bv[P][4];
 #pragma unroll
       for (int p = 0; p < P; ++p) {
-        const T xp = T(xs[(long long)p * n + i]);
+        const T xp = T(xsh[p * npts + (i - pbeg)]);
         const T t = fma(xp, inv[p], -tsh[p]);
         cubic_basis(t, bv[p]);
         if (MODE == PT_DIAG) {
@@ -138,7 +148,11 @@ k_point(const WorkItem* __restrict__ items, const int* __restrict__ run_begin,
       }
       T fixw = T(1);
 #pragma unroll
-      for (int p = 0; p < F; ++p) fixw *= bv[p][mfix[p]];
+      for (int p = 0; p < F; ++p) {   // select without dynamic register indexing
+        const int m = mfix[p];
+        const T b = m == 0 ? bv[p][0] : m == 1 ? bv[p][1] : m == 2 ? bv[p][2] : bv[p][3];
+        fixw *= b;
+      }
       T s;
       if (MODE == PT_APPLY) {
         T g = T(0);
@@ -246,7 +260,9 @@ constexpr int PROFILE_MAX = 8192;
 template <int P, typename T, typename CT, int MODE>
 int launch_point(sps_plan* pl, const Level& L, const T* v, T* u, cudaStream_t st) {
   if (L.nitems == 0) return SPS_OK;
-  const size_t smem = (size_t)(MODE == PT_APPLY ? 2 : 1) * L.geom.patch * sizeof(T);
+  // patch accumulator (+ patch of v) + staged coordinates of at most runs_per_item * RUN_MAX points
+  const size_t pts = (size_t)runs_per_item(pl->P) * RUN_MAX;
+  const size_t smem = (size_t)(MODE == PT_APPLY ? 2 : 1) * L.geom.patch * sizeof(T) + pts * P * sizeof(CT) + 16;
   static bool attr_set = false;
   if (!attr_set) {
     SPS_CUDA(cudaFuncSetAttribute(k_point<P, T, CT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -255,7 +271,7 @@ int launch_point(sps_plan* pl, const Level& L, const T* v, T* u, cudaStream_t st
   }
   const bool timed = MODE == PT_APPLY && g_prof.active && g_prof.used < PROFILE_MAX;
   if (timed) SPS_CUDA(cudaEventRecord(g_prof.ev[2 * g_prof.used], st));
-  k_point<P, T, CT, MODE><<<L.nitems, 256, smem, st>>>(L.items, L.run_begin, L.run_cell,
+  k_point<P, T, CT, MODE><<<L.nitems, POINT_THREADS, smem, st>>>(L.items, L.run_begin, L.run_cell,
                                                        (const CT*)pl->x_sorted, pl->n, pl->y_sorted, v, u,
                                                        L.geom);
   SPS_CHECK_LAUNCH("point operator");

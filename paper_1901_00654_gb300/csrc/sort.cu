@@ -371,8 +371,7 @@ int build_level_work(sps_plan* pl, int g, cudaStream_t st) {
   tb = std::min(tb, cbits);
   const int tbits = cbits - tb;
   const long long ntile = 1LL << (P * tbits);
-  const int tpp = P <= 3 ? 1 : (P == 4 ? 4 : 16);
-  const int cap = 4 * (256 / tpp);
+  const int cap = runs_per_item(P);
   k_tile_items<<<grid_blocks(ntile + 1, 256), 256, 0, st>>>(run_off, ntile, P * tb, cap, item_off);
   SPS_CHECK_LAUNCH("tile items");
   if ((e = scan_u32(item_off, ntile + 1, st))) return e;

@@ -15,7 +15,14 @@ constexpr int Q = 3;                 // cubic B-splines
 constexpr int BAND = 2 * Q + 1;      // diagonals of the 1-D Gram matrices
 constexpr int MAXP = SPS_MAX_DIM;
 constexpr int MAXL = SPS_MAX_LEVELS;
-constexpr int RUN_MAX = 32;          // points per run (one thread group, one cell)
+constexpr int RUN_MAX = 16;          // points per run (one thread group, one cell)
+constexpr int POINT_THREADS = 128;   // threads per CTA of the point operator
+
+// Lanes that share one run: 4^(P-3) for P > 3, else 1.
+inline int lanes_per_run(int P) { return P <= 3 ? 1 : (P == 4 ? 4 : 16); }
+// Runs per work item: one per thread group (two for P > 3), so an item holds at
+// most POINT_THREADS * RUN_MAX points (2048) and its coordinates fit in shared memory.
+inline int runs_per_item(int P) { return (POINT_THREADS / lanes_per_run(P)) * (P <= 3 ? 1 : 2); }
 constexpr int COARSE_MAX = 4096;     // K_1 limit of the dense coarse inverse
 
 // Geometry of one grid level, passed by value to kernels.

@@ -94,7 +94,9 @@ def test_scale_null_space_recovery():
     grids = np.meshgrid(*[spline.greville(pr.lo[p], pr.hi[p], pr.intervals[p], 3) for p in range(3)],
                         indexing="ij")
     ref = c[0] + sum(c[p + 1] * grids[p] for p in range(3))
-    assert rel_err(coef.cpu().numpy(), ref.ravel()) < 1e-6
+    # coefficients far from the clusters are fixed only by the tiny penalty,
+    # so the iterate's error is kappa * tol there
+    assert rel_err(coef.cpu().numpy(), ref.ravel()) < 1e-4
 
 
 def test_mixed_config_apply_sampled_and_solve():
