@@ -338,19 +338,155 @@ def run_ours(args, pr):
         dist.destroy_process_group()
 
 
+def run_apply_only(args, pr):
+    """Set up the workload once and apply the finest-level point operator
+    `--reps` times in FP64 and FP32 (the kernel that ncu captures); prints the
+    event-timed average per launch."""
+    import torch
+
+    from paper_1901_00654_gb300 import binding as B
+    from paper_1901_00654_gb300 import build as libbuild
+    libbuild.build_library()
+    x_d = torch.from_numpy(np.ascontiguousarray(pr.x)).cuda()
+    y_d = torch.from_numpy(np.ascontiguousarray(pr.y)).cuda()
+    out = {"workload": workload_desc(pr)}
+    with B.Plan(pr.P, pr.intervals, pr.levels, pr.lam, pr.lo, pr.hi) as plan:
+        plan.set_points(x_d, y_d)
+        v = torch.randn(plan.K, dtype=torch.float64, device="cuda")
+        u = torch.zeros_like(v)
+        for prec, name in ((B.SPS_PREC_FP64, "fp64"), (B.SPS_PREC_MIXED, "fp32")):
+            B.sps_point_apply(plan.h, pr.levels, prec, v, u)
+            torch.cuda.synchronize()
+            B.sps_profile_begin()
+            for _ in range(args.reps):
+                B.sps_point_apply(plan.h, pr.levels, prec, v, u)
+            torch.cuda.synchronize()
+            ms, cnt = B.sps_profile_end()
+            out[name + "_ms_per_launch"] = ms / max(cnt, 1)
+    print(json.dumps(out), flush=True)
+
+
+def run_batched(args):
+    """The batched workload: 512 independent problems solved by one persistent
+    graph-captured launch (plans resident), against the same problems solved
+    one after the other by the plain FP64 solver."""
+    import torch
+
+    from paper_1901_00654_gb300 import binding as B
+    from paper_1901_00654_gb300 import build as libbuild
+    libbuild.build_library()
+    probs = W.batched(count=args.batch_count)
+    plans = []
+    t0 = time.perf_counter()
+    for pr in probs:
+        pl = B.Plan(pr.P, pr.intervals, pr.levels, pr.lam, pr.lo, pr.hi, precision=B.SPS_PREC_MIXED)
+        pl.set_points(torch.from_numpy(pr.x).cuda(), torch.from_numpy(pr.y).cuda())
+        plans.append(pl)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    coefs = [torch.zeros(pl.K, dtype=torch.float64, device="cuda") for pl in plans]
+    hs = [pl.h for pl in plans]
+    tol = args.batch_tol
+    for _ in range(max(args.warmup, 1)):
+        B.sps_solve_batch(hs, coefs, tol, check=False)
+    times = []
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = B.sps_solve_batch(hs, coefs, tol, check=False)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    bt = statistics.median(times)
+    its = [r.iterations for r in res]
+    ok = sum(r.status == B.SPS_OK for r in res)
+    # sequential plain FP64 on a sample of the same problems (the full set takes minutes)
+    seq_n = min(args.seq_sample, len(probs))
+    seq_t = 0.0
+    for pr in probs[:seq_n]:
+        with B.Plan(pr.P, pr.intervals, pr.levels, pr.lam, pr.lo, pr.hi) as p64:
+            p64.set_points(torch.from_numpy(pr.x).cuda(), torch.from_numpy(pr.y).cuda())
+            c = torch.zeros(p64.K, dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            p64.solve(tol, c, check=False)
+            torch.cuda.synchronize()
+            seq_t += time.perf_counter() - t0
+    for pl in plans:
+        pl.close()
+    line = {"metric": METRIC, "value": len(probs) / bt, "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": max(args.warmup, 1), "ms_per_step": bt * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "batched: %d problems P in {1,2,3}, K <= 40k, n log-uniform [1e3,1e5], "
+                                   "lambda log-uniform [1e-5,1e-1], tol %g, plans resident" % (len(probs), tol)},
+            "converged": ok, "iterations_median": statistics.median(its), "iterations_max": max(its),
+            "setup_s_all_plans": setup_s,
+            "sequential_plain_fp64": {"solves_per_s": seq_n / seq_t, "sample": seq_n}}
+    print(json.dumps(line), flush=True)
+
+
+def run_serving(args):
+    """Poisson request trace through the continuous-batching server, then the
+    same requests one at a time with the plain FP64 solver."""
+    import torch  # noqa: F401
+
+    from paper_1901_00654_gb300 import binding as B
+    from paper_1901_00654_gb300 import build as libbuild
+    from paper_1901_00654_gb300 import serving
+    libbuild.build_library()
+    trace = W.serving_trace(count=args.serve_count, n_hi=args.serve_n_hi)
+    srv = serving.Server(slots=args.slots, tol=args.serve_tol)
+    try:
+        warm = W.serving_trace(seed=99, count=4, n_hi=2e4, P_choices=(2, 3))
+        srv.run(warm, time_scale=0.0)
+        stats = srv.run(trace)
+    finally:
+        srv.close()
+    mixed = stats.summary()
+    seq = serving.Server(slots=1, precision=B.SPS_PREC_FP64, tol=args.serve_tol)
+    try:
+        sstats = seq.run(trace)
+    finally:
+        seq.close()
+    plain = sstats.summary()
+    line = {"metric": METRIC, "value": mixed["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
+            "steps": len(trace), "warmup": 4, "ms_per_step": 1e3 / max(mixed["solves_per_s"], 1e-12),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": "serving: %d Poisson requests at 200/s, P in {2,3,4,5}, n log-uniform [1e4,%g], "
+                                   "tol %g, %d slots, 120 GB budget" % (len(trace), args.serve_n_hi, args.serve_tol,
+                                                                       args.slots)},
+            "served": mixed, "sequential_plain_fp64": plain}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="scale", choices=["scale", "pr1", "mixed"])
+    ap.add_argument("--config", default="scale", choices=["scale", "pr1", "mixed", "batched", "serving"])
+    ap.add_argument("--apply-only", action="store_true", help="time the finest-level point operator only")
+    ap.add_argument("--reps", type=int, default=10)
+    ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--batch-tol", type=float, default=1e-8)
+    ap.add_argument("--seq-sample", type=int, default=32)
+    ap.add_argument("--serve-count", type=int, default=200)
+    ap.add_argument("--serve-n-hi", type=float, default=2e6)
+    ap.add_argument("--serve-tol", type=float, default=1e-6)
+    ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--n", type=int, default=None, help="override the number of points")
     ap.add_argument("--ref-sample", type=int, default=200_000)
     ap.add_argument("--ref-iters", type=int, default=12, help="iterations assumed by the reference arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    if args.config == "batched":
+        return run_batched(args)
+    if args.config == "serving":
+        return run_serving(args)
     pr = make_problem(args.config, args.n)
+    if args.apply_only:
+        return run_apply_only(args, pr)
     if args.impl == "reference":
         run_reference(args, pr)
     else:

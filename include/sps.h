@@ -86,6 +86,11 @@ typedef struct sps_options {
     double replace_ratio;  /* MIXED: recompute the FP64 residual when |r| has
                               dropped by this factor since the last recompute
                               (default 1e-2) */
+    int    hybrid;         /* 1 (default): levels between the coarsest and the
+                              finest whose assembled (2q+1)^P-stencil matrix is
+                              cheaper to apply than a point sweep are assembled
+                              once in sps_set_points (same matrix A_g); 0: every
+                              level matrix free */
 } sps_options;
 
 typedef struct sps_result {
@@ -133,11 +138,29 @@ SPS_API int sps_set_points(sps_plan* plan, int64_t n, const void* x, const void*
  * Errors: SPS_ESTATE (no points), SPS_EINVAL, SPS_ENOCONV, SPS_EBREAKDOWN, SPS_ECUDA. */
 SPS_API int sps_solve(sps_plan* plan, double* coef, int mem, double tol, sps_result* res, void* stream);
 
+/* Change lambda of a plan; takes effect at the next sps_set_points (which
+ * recomputes the right-hand side, diagonals, coarse matrix and damping).
+ * Lets a pool of plans of one grid shape serve problems with different
+ * lambda without new allocations.  Errors: SPS_EINVAL. */
+SPS_API int sps_set_lambda(sps_plan* plan, double lambda);
+
 /* Release the plan and all of its device memory.  NULL is accepted. */
 SPS_API int sps_destroy(sps_plan* plan);
 
 /* Thread-local message of the last failure (never NULL). */
 SPS_API const char* sps_last_error(void);
+
+/* Solve `count` independent problems in ONE persistent kernel launch captured
+ * in a CUDA graph: each CTA pops whole problems from a device queue (largest
+ * first) and runs the mixed-precision flexible PCG of Algorithm 8 with the
+ * FP32 V-cycle of Algorithm 7 entirely inside the CTA.  plans[i] must have
+ * P <= 3 and points set; coefs[i] receives K_G(i) doubles in `mem`; tol is
+ * shared; results may be NULL (else `count` entries).  Each plan's buffers are
+ * used, so a plan must not be in another call at the same time.  Returns the
+ * first non-OK status among the problems (all are attempted).  Synchronises
+ * `stream`. */
+SPS_API int sps_solve_batch(sps_plan* const* plans, int count, double* const* coefs, int mem, double tol,
+                            sps_result* results, void* stream);
 
 /* ---------------- component entry points (each one step of the solve) ----------------
  * All vectors are doubles in `mem`; `prec` selects the FP64 kernels

@@ -29,13 +29,13 @@ EXPORTED = ["sps_default_options", "sps_plan_create", "sps_set_points", "sps_sol
             "sps_last_error", "sps_coef_count", "sps_apply", "sps_penalty_apply", "sps_diag", "sps_rhs",
             "sps_prolong", "sps_restrict", "sps_coarse_solve", "sps_vcycle", "sps_get_sort", "sps_get_omega",
             "sps_set_omega", "sps_probe_fma_rate", "sps_point_apply", "sps_launch_count",
-            "sps_profile_begin", "sps_profile_end"]
+            "sps_profile_begin", "sps_profile_end", "sps_solve_batch", "sps_set_lambda"]
 
 
 class sps_options(C.Structure):
     _fields_ = [("precision", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int), ("omega", C.c_double),
                 ("power_iters", C.c_int), ("max_iter", C.c_int), ("warm_start", C.c_int), ("tile", C.c_int),
-                ("replace_ratio", C.c_double)]
+                ("replace_ratio", C.c_double), ("hybrid", C.c_int)]
 
 
 class sps_result(C.Structure):
@@ -80,6 +80,8 @@ def load(path: str | None = None) -> C.CDLL:
         "sps_launch_count": (I, [C.POINTER(C.c_uint64)]),
         "sps_profile_begin": (I, []),
         "sps_profile_end": (I, [C.POINTER(D), C.POINTER(C.c_uint64)]),
+        "sps_solve_batch": (I, [C.POINTER(P), I, C.POINTER(P), I, D, C.POINTER(sps_result), P]),
+        "sps_set_lambda": (I, [P, D]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -167,6 +169,26 @@ def sps_solve(plan, coef, tol, stream=None, check=True) -> sps_result:
     if check:
         _check(code, "sps_solve")
     return res
+
+
+def sps_solve_batch(plans, coefs, tol, stream=None, check=True) -> list:
+    """plans: list of plan handles; coefs: list of numpy arrays or CUDA tensors (one per plan)."""
+    n = len(plans)
+    ph = (C.c_void_p * n)(*[p.value if isinstance(p, C.c_void_p) else p for p in plans])
+    bufs = [_buf(c) for c in coefs]
+    mems = {m for _, m in bufs}
+    if len(mems) != 1:
+        raise ValueError("all coefficient buffers must live in the same memory")
+    ch = (C.c_void_p * n)(*[b[0].value for b in bufs])
+    res = (sps_result * n)()
+    code = lib().sps_solve_batch(ph, n, ch, mems.pop(), tol, res, _stream(stream))
+    if check:
+        _check(code, "sps_solve_batch")
+    return list(res)
+
+
+def sps_set_lambda(plan, lam) -> None:
+    _check(lib().sps_set_lambda(plan, lam), "sps_set_lambda")
 
 
 def sps_destroy(plan) -> None:

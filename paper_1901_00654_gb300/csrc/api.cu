@@ -200,6 +200,9 @@ int copy_out(double* dst, const double* src, long long n, int mem, cudaStream_t 
 // ---- operator on one level: u = (Phi_g'Phi_g + lambda Lambda_g) v --------------
 template <typename T>
 int apply_level(sps_plan* pl, int g, const T* v, T* u, cudaStream_t st) {
+  const Level& L = pl->lev[g - 1];
+  if ((sizeof(T) == 8 && L.st_d) || (sizeof(T) == 4 && L.st_f))
+    return stencil_apply<T>(pl, g, v, u, st);             // assembled coarse level
   SPS_TRY(penalty_apply<T>(pl, g, v, u, pl->lam, st));    // u = lambda Lambda v
   return point_op<T>(pl, g, PT_APPLY, v, u, st);          // u += Phi'Phi v
 }
@@ -281,6 +284,49 @@ int estimate_omega(sps_plan* pl, int g, cudaStream_t st) {
     return SPS_EBREAKDOWN;
   }
   L.omega = 4.0 / (3.0 * lmax);
+  return SPS_OK;
+}
+
+// Levels strictly between the coarsest and the finest are assembled in
+// stencil form when one sparse matrix-vector product over the (2q+1)^P
+// stencil moves fewer bytes than the point sweep costs in arithmetic:
+//   S K_g sizeof(T) / (0.6 * 6.8 TB/s)  <  n * 2 (q+1)^P / (0.3 * FMA rate of T),
+// with a budget of 8 GB per level.  The assembled matrix is exactly A_g
+// (same sums, another order), so the method is unchanged; the finest level
+// always stays matrix free.
+int assemble_coarse_levels(sps_plan* pl, cudaStream_t st) {
+  if (!pl->opt.hybrid) return SPS_OK;
+  const int P = pl->P;
+  long long S = 1, loc = 1;
+  for (int p = 0; p < P; ++p) {
+    S *= BAND;
+    loc *= Q + 1;
+  }
+  const bool mixed = pl->opt.precision == SPS_PREC_MIXED;
+  const double tsize = mixed ? 4.0 : 8.0;
+  const double rate = mixed ? 38.7e12 : 0.53e12;
+  for (int g = 2; g < pl->G; ++g) {
+    Level& L = pl->lev[g - 1];
+    const long long K = L.geom.K;
+    const double spmv_s = (double)S * K * tsize / (0.6 * 6.8e12);
+    const double sweep_s = (double)pl->n * 2.0 * loc / (0.3 * rate);
+    const bool want = spmv_s < sweep_s && (double)S * K * 8.0 <= 8e9;
+    if (!want) {
+      cudaFree(L.st_d);
+      cudaFree(L.st_f);
+      L.st_d = nullptr;
+      L.st_f = nullptr;
+      continue;
+    }
+    L.S = (int)S;
+    if (!L.st_d) SPS_TRY(alloc(&L.st_d, S * K));
+    if (mixed && !L.st_f) SPS_TRY(alloc(&L.st_f, S * K));
+    SPS_TRY(stencil_assemble(pl, g, st));
+    if (mixed) {   // the FP32 V-cycle reads the FP32 copy only
+      cudaFree(L.st_d);
+      L.st_d = nullptr;
+    }
+  }
   return SPS_OK;
 }
 
@@ -506,6 +552,7 @@ void sps_default_options(sps_options* opt) {
   opt->warm_start = 0;
   opt->tile = 0;
   opt->replace_ratio = 1e-2;
+  opt->hybrid = 1;
 }
 
 const char* sps_last_error(void) { return g_last_error.c_str(); }
@@ -675,6 +722,16 @@ int sps_plan_create(sps_plan** out, int P, int q, const int* intervals, const do
   return SPS_OK;
 }
 
+int sps_set_lambda(sps_plan* pl, double lambda) {
+  if (!pl || !(lambda >= 0.0) || !std::isfinite(lambda)) {
+    set_error("invalid plan or lambda");
+    return SPS_EINVAL;
+  }
+  pl->lam = lambda;
+  pl->have_points = false;   // the diagonals and the coarse matrix depend on lambda
+  return SPS_OK;
+}
+
 int sps_destroy(sps_plan* pl) {
   if (!pl) return SPS_OK;
   for (int g = 0; g < MAXL; ++g) {
@@ -682,6 +739,8 @@ int sps_destroy(sps_plan* pl) {
     free_vecs(L.d);
     free_vecs(L.f);
     cudaFree(L.diag);
+    cudaFree(L.st_d);
+    cudaFree(L.st_f);
     cudaFree(L.run_begin);
     cudaFree(L.run_cell);
     cudaFree(L.items);
@@ -784,6 +843,7 @@ int sps_set_points(sps_plan* pl, int64_t n, const void* x, const void* y, int dt
   SPS_TRY(read_scalars(pl, st));
   pl->rhs_norm = std::sqrt(pl->host_scal[S_TMP]);
   SPS_TRY(coarse_assemble(pl, st));
+  SPS_TRY(assemble_coarse_levels(pl, st));
   for (int g = 2; g <= G; ++g) {
     if (pl->opt.omega > 0.0) pl->lev[g - 1].omega = pl->opt.omega;
     else SPS_TRY(estimate_omega(pl, g, st));
@@ -823,6 +883,26 @@ int sps_solve(sps_plan* pl, double* coef, int mem, double tol, sps_result* res_o
   res.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   if (res_out) *res_out = res;
   return res.status;
+}
+
+int sps_solve_batch(sps_plan* const* plans, int count, double* const* coefs, int mem, double tol,
+                    sps_result* results, void* stream) {
+  if (!plans || !coefs || count < 1 || !(tol > 0.0) || (mem != SPS_MEM_HOST && mem != SPS_MEM_DEVICE)) {
+    set_error("invalid batch arguments");
+    return SPS_EINVAL;
+  }
+  for (int i = 0; i < count; ++i) {
+    SPS_TRY(check_plan_points(plans[i]));
+    if (plans[i]->P > 3 || !coefs[i]) {
+      set_error("batched solves take P <= 3 and a coefficient buffer per problem");
+      return SPS_EINVAL;
+    }
+    if (plans[i]->rhs_norm == 0.0) {
+      set_error("a problem of the batch has a zero right-hand side");
+      return SPS_EINVAL;
+    }
+  }
+  return solve_batch(plans, count, coefs, mem, tol, results, as_stream(stream));
 }
 
 int sps_coef_count(const sps_plan* pl, int level, int64_t* K) {

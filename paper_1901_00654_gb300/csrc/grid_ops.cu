@@ -143,7 +143,10 @@ __global__ void k_restrict_sweep(long long Kout, long long inner, int Jin, int J
 // grid solver).  One CTA takes a contiguous range of runs (points of one cell)
 // and a block of CB local columns; each thread owns 16 entries of the local
 // (q+1)^P x CB block of sum_i b_i b_i' in FP64 registers.  Products use TP.
-template <int P, typename TP>
+// STENCIL = true writes the same sums into the offset-major stencil form
+// A_st[s * K + k] (s = the (2q+1)^P offset of column l from row k) used for
+// the assembled coarse levels.
+template <int P, typename TP, bool STENCIL>
 __global__ void __launch_bounds__(256) k_coarse_phi(const int* __restrict__ run_begin,
                                                     const unsigned long long* __restrict__ run_cell, int nruns,
                                                     int runs_per_cta, const void* __restrict__ xs_raw, int x_f64,
@@ -171,14 +174,19 @@ __global__ void __launch_bounds__(256) k_coarse_phi(const int* __restrict__ run_
       if (le >= LOC * CB) break;
       const int row = le / CB, col = le % CB + cb0;
       long long gr = 0, gc = 0;
-      int rr = row, cc = col;
+      int rr = row, cc = col, so = 0, sw = 1;
       for (int p = P - 1; p >= 0; --p) {
         gr += (long long)(c[p] + (rr & 3)) * geom.stride[p];
         gc += (long long)(c[p] + (cc & 3)) * geom.stride[p];
+        so += ((cc & 3) - (rr & 3) + Q) * sw;
+        sw *= BAND;
         rr >>= 2;
         cc >>= 2;
       }
-      if (acc[e] != 0.0) atomicAdd(&A1[gr * geom.K + gc], acc[e]);
+      if (acc[e] != 0.0) {
+        if (STENCIL) atomicAdd(&A1[(long long)so * geom.K + gr], acc[e]);
+        else atomicAdd(&A1[gr * geom.K + gc], acc[e]);
+      }
       acc[e] = 0.0;
     }
   };
@@ -258,6 +266,71 @@ __global__ void k_coarse_penalty(LevelGeom geom, const double* __restrict__ band
       boff += 3LL * Jp * BAND;
     }
     if (nz) A1[e] += lam * d2;
+  }
+}
+
+// + lambda Lambda_g in stencil form: entry (k, k + offset s).
+__global__ void k_stencil_penalty(LevelGeom geom, const double* __restrict__ band, double lam,
+                                  double* __restrict__ A, int S) {
+  const long long K = geom.K;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)S * K;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int s = (int)(e / K);
+    const long long k = e - (long long)s * K;
+    double d0 = 1.0, d1 = 0.0, d2 = 0.0;
+    long long boff = 0;
+    int ss = s;
+    int o[MAXP];
+    for (int p = geom.P - 1; p >= 0; --p) {
+      o[p] = ss % BAND - Q;
+      ss /= BAND;
+    }
+    bool ok = true;
+    for (int p = 0; p < geom.P; ++p) {
+      const int Jp = geom.J[p];
+      const int j = (int)((k / geom.stride[p]) % Jp);
+      if (j + o[p] < 0 || j + o[p] >= Jp) { ok = false; break; }
+      const double m = band[boff + (long long)j * BAND + o[p] + Q];
+      const double e1 = band[boff + ((long long)Jp + j) * BAND + o[p] + Q];
+      const double e2 = band[boff + (2LL * Jp + j) * BAND + o[p] + Q];
+      d2 = m * d2 + 2.0 * e1 * d1 + e2 * d0;
+      d1 = m * d1 + e1 * d0;
+      d0 = m * d0;
+      boff += 3LL * Jp * BAND;
+    }
+    if (ok) A[e] += lam * d2;
+  }
+}
+
+__global__ void k_d2f_scaled(const double* __restrict__ a, float* __restrict__ b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+
+// u = A_st v for an assembled level: one thread per row, offsets in the
+// outer loop so that the matrix (offset-major) and v are read coalesced.
+template <typename T>
+__global__ void k_stencil_spmv(const T* __restrict__ A, LevelGeom geom, int S, const T* __restrict__ v,
+                               T* __restrict__ u) {
+  const long long K = geom.K;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < K; k += (long long)gridDim.x * blockDim.x) {
+    int j[MAXP];
+    for (int p = 0; p < geom.P; ++p) j[p] = (int)((k / geom.stride[p]) % geom.J[p]);
+    T acc = T(0);
+    for (int s = 0; s < S; ++s) {
+      int ss = s;
+      long long off = 0;
+      bool ok = true;
+      for (int p = geom.P - 1; p >= 0; --p) {
+        const int o = ss % BAND - Q;
+        ss /= BAND;
+        const int jj = j[p] + o;
+        ok = ok && jj >= 0 && jj < geom.J[p];
+        off += (long long)o * geom.stride[p];
+      }
+      if (ok) acc = fma(A[(long long)s * K + k], v[k + off], acc);
+    }
+    u[k] = acc;
   }
 }
 
@@ -556,28 +629,43 @@ int restrict_res(sps_plan* pl, int g, const T* f, const T* fb, T* c, cudaStream_
 template int restrict_res<double>(sps_plan*, int, const double*, const double*, double*, cudaStream_t);
 template int restrict_res<float>(sps_plan*, int, const float*, const float*, float*, cudaStream_t);
 
-template <int P>
-int coarse_phi_launch(sps_plan* pl, cudaStream_t st) {
-  Level& L = pl->lev[0];
+template <int P, typename TP, bool STENCIL>
+int phi_assembly_launch(sps_plan* pl, const Level& L, double* out, cudaStream_t st) {
   constexpr int LOC = 1 << (2 * P);
   constexpr int CB = P <= 3 ? LOC : (P == 4 ? 16 : 4);
-  const bool fp32 = pl->opt.precision == SPS_PREC_MIXED || P >= 4;
   const int rpc = 8;
-  dim3 grid((L.nruns + rpc - 1) / rpc, LOC / CB);
   if (L.nruns == 0) return SPS_OK;
-  if (fp32) {
-    const size_t smem = sizeof(float) * (RUN_MAX * LOC + RUN_MAX * P * 4);
-    SPS_CUDA(cudaFuncSetAttribute(k_coarse_phi<P, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    k_coarse_phi<P, float><<<grid, 256, smem, st>>>(L.run_begin, L.run_cell, L.nruns, rpc, pl->x_sorted,
-                                                   pl->dtype == SPS_F64, pl->n, L.geom, pl->coarse_inv);
-  } else {
-    const size_t smem = sizeof(double) * (RUN_MAX * LOC + RUN_MAX * P * 4);
-    SPS_CUDA(cudaFuncSetAttribute(k_coarse_phi<P, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    k_coarse_phi<P, double><<<grid, 256, smem, st>>>(L.run_begin, L.run_cell, L.nruns, rpc, pl->x_sorted,
-                                                    pl->dtype == SPS_F64, pl->n, L.geom, pl->coarse_inv);
-  }
-  SPS_CHECK_LAUNCH("coarse assembly");
+  dim3 grid((L.nruns + rpc - 1) / rpc, LOC / CB);
+  const size_t smem = sizeof(TP) * (RUN_MAX * LOC + RUN_MAX * P * 4);
+  SPS_CUDA(cudaFuncSetAttribute(k_coarse_phi<P, TP, STENCIL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                200 * 1024));
+  k_coarse_phi<P, TP, STENCIL><<<grid, 256, smem, st>>>(L.run_begin, L.run_cell, L.nruns, rpc, pl->x_sorted,
+                                                        pl->dtype == SPS_F64, pl->n, L.geom, out);
+  SPS_CHECK_LAUNCH("Phi'Phi assembly");
   return SPS_OK;
+}
+
+// Phi_g'Phi_g assembled into `out` (dense K x K, or stencil form), FP32
+// products (with FP64 accumulation) in the mixed mode and for P >= 4.
+template <int P>
+int coarse_phi_launch(sps_plan* pl, const Level& L, double* out, bool stencil, cudaStream_t st) {
+  const bool fp32 = pl->opt.precision == SPS_PREC_MIXED || P >= 4;
+  if (fp32) return stencil ? phi_assembly_launch<P, float, true>(pl, L, out, st)
+                           : phi_assembly_launch<P, float, false>(pl, L, out, st);
+  return stencil ? phi_assembly_launch<P, double, true>(pl, L, out, st)
+                 : phi_assembly_launch<P, double, false>(pl, L, out, st);
+}
+
+int phi_assembly(sps_plan* pl, const Level& L, double* out, bool stencil, cudaStream_t st) {
+  switch (pl->P) {
+    case 1: return coarse_phi_launch<1>(pl, L, out, stencil, st);
+    case 2: return coarse_phi_launch<2>(pl, L, out, stencil, st);
+    case 3: return coarse_phi_launch<3>(pl, L, out, stencil, st);
+    case 4: return coarse_phi_launch<4>(pl, L, out, stencil, st);
+    case 5: return coarse_phi_launch<5>(pl, L, out, stencil, st);
+  }
+  set_error("unsupported dimension");
+  return SPS_EINVAL;
 }
 
 // Assemble A_1 into coarse_inv and invert it in place.
@@ -585,14 +673,7 @@ int coarse_assemble(sps_plan* pl, cudaStream_t st) {
   Level& L = pl->lev[0];
   const long long K = L.geom.K;
   SPS_CUDA(cudaMemsetAsync(pl->coarse_inv, 0, sizeof(double) * K * K, st));
-  int e = SPS_OK;
-  switch (pl->P) {
-    case 1: e = coarse_phi_launch<1>(pl, st); break;
-    case 2: e = coarse_phi_launch<2>(pl, st); break;
-    case 3: e = coarse_phi_launch<3>(pl, st); break;
-    case 4: e = coarse_phi_launch<4>(pl, st); break;
-    case 5: e = coarse_phi_launch<5>(pl, st); break;
-  }
+  int e = phi_assembly(pl, L, pl->coarse_inv, false, st);
   if (e) return e;
   k_coarse_penalty<<<grid_blocks(K * K, EW_THREADS), EW_THREADS, 0, st>>>(L.geom, L.d.band, pl->lam,
                                                                           pl->coarse_inv);
@@ -615,6 +696,37 @@ int coarse_assemble(sps_plan* pl, cudaStream_t st) {
   SPS_CHECK_LAUNCH("coarse cast");
   return SPS_OK;
 }
+
+// Assemble A_g = Phi_g'Phi_g + lambda Lambda_g of level g in stencil form
+// (FP64 accumulation; FP32 copy for the mixed V-cycle).
+int stencil_assemble(sps_plan* pl, int g, cudaStream_t st) {
+  Level& L = pl->lev[g - 1];
+  const long long K = L.geom.K;
+  const int S = L.S;
+  SPS_CUDA(cudaMemsetAsync(L.st_d, 0, sizeof(double) * S * K, st));
+  int e = phi_assembly(pl, L, L.st_d, true, st);
+  if (e) return e;
+  k_stencil_penalty<<<grid_blocks((long long)S * K, EW_THREADS), EW_THREADS, 0, st>>>(L.geom, L.d.band, pl->lam,
+                                                                                     L.st_d, S);
+  SPS_CHECK_LAUNCH("stencil penalty");
+  if (L.st_f) {
+    k_d2f_scaled<<<grid_blocks((long long)S * K, EW_THREADS), EW_THREADS, 0, st>>>(L.st_d, L.st_f, (long long)S * K);
+    SPS_CHECK_LAUNCH("stencil cast");
+  }
+  return SPS_OK;
+}
+
+template <typename T>
+int stencil_apply(sps_plan* pl, int g, const T* v, T* u, cudaStream_t st) {
+  Level& L = pl->lev[g - 1];
+  const T* A = nullptr;
+  if constexpr (sizeof(T) == 8) A = (const T*)L.st_d; else A = (const T*)L.st_f;
+  k_stencil_spmv<T><<<grid_blocks(L.geom.K, EW_THREADS), EW_THREADS, 0, st>>>(A, L.geom, L.S, v, u);
+  SPS_CHECK_LAUNCH("stencil apply");
+  return SPS_OK;
+}
+template int stencil_apply<double>(sps_plan*, int, const double*, double*, cudaStream_t);
+template int stencil_apply<float>(sps_plan*, int, const float*, float*, cudaStream_t);
 
 template <typename T>
 int coarse_solve(sps_plan* pl, const T* r, T* e, cudaStream_t st) {

@@ -352,14 +352,19 @@ int build_level_work(sps_plan* pl, int g, cudaStream_t st) {
   unsigned int nruns = 0;
   SPS_CUDA(cudaMemcpyAsync(&nruns, run_off + ncell, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
   SPS_CUDA(cudaStreamSynchronize(st));
-  if (L.run_begin) cudaFree(L.run_begin);
-  if (L.run_cell) cudaFree(L.run_cell);
-  L.run_begin = nullptr;
-  L.run_cell = nullptr;
-  if (cudaMalloc(&L.run_begin, sizeof(int) * (nruns + 1)) != cudaSuccess ||
-      cudaMalloc(&L.run_cell, sizeof(unsigned long long) * std::max(nruns, 1u)) != cudaSuccess) {
-    set_error("allocation of run lists failed");
-    return SPS_ENOMEM;
+  if ((int)nruns > L.run_cap) {   // grow only: cudaFree would synchronise the whole device
+    cudaFree(L.run_begin);
+    cudaFree(L.run_cell);
+    L.run_begin = nullptr;
+    L.run_cell = nullptr;
+    L.run_cap = 0;
+    const unsigned int cap = nruns + nruns / 4 + 16;
+    if (cudaMalloc(&L.run_begin, sizeof(int) * (cap + 1)) != cudaSuccess ||
+        cudaMalloc(&L.run_cell, sizeof(unsigned long long) * cap) != cudaSuccess) {
+      set_error("allocation of run lists failed");
+      return SPS_ENOMEM;
+    }
+    L.run_cap = (int)cap;
   }
   L.nruns = (int)nruns;
   k_fill_runs<<<grid_blocks(ncell, 256), 256, 0, st>>>(pl->keys, pl->n, ncell, sh, P, cbits, run_off,
@@ -378,11 +383,16 @@ int build_level_work(sps_plan* pl, int g, cudaStream_t st) {
   unsigned int nitems = 0;
   SPS_CUDA(cudaMemcpyAsync(&nitems, item_off + ntile, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
   SPS_CUDA(cudaStreamSynchronize(st));
-  if (L.items) cudaFree(L.items);
-  L.items = nullptr;
-  if (cudaMalloc(&L.items, sizeof(WorkItem) * std::max(nitems, 1u)) != cudaSuccess) {
-    set_error("allocation of work items failed");
-    return SPS_ENOMEM;
+  if ((int)nitems > L.item_cap) {
+    cudaFree(L.items);
+    L.items = nullptr;
+    L.item_cap = 0;
+    const unsigned int cap = nitems + nitems / 4 + 16;
+    if (cudaMalloc(&L.items, sizeof(WorkItem) * cap) != cudaSuccess) {
+      set_error("allocation of work items failed");
+      return SPS_ENOMEM;
+    }
+    L.item_cap = (int)cap;
   }
   L.nitems = (int)nitems;
   k_fill_items<<<grid_blocks(ntile, 256), 256, 0, st>>>(run_off, item_off, ntile, P * tb, cap, P, tbits, tb,

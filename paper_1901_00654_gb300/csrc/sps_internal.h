@@ -62,11 +62,17 @@ struct Level {
   // runs: points [run_begin[r], run_begin[r+1]) share one level cell run_cell[r]
   int* run_begin = nullptr;
   unsigned long long* run_cell = nullptr;   // 12 bits per dimension
-  int nruns = 0;
+  int nruns = 0, run_cap = 0;
   WorkItem* items = nullptr;
-  int nitems = 0;
+  int nitems = 0, item_cap = 0;
   double omega = 0.0;
   double* diag = nullptr;                   // FP64 diag(A_g)
+  // assembled operator of a coarse level, offset-major stencil form
+  // A_st[s * K + k] = A_g(k, k + offset_s), s < S = (2q+1)^P; null when the
+  // level is applied matrix free
+  int S = 0;
+  double* st_d = nullptr;
+  float* st_f = nullptr;
   LevelVecs<double> d;
   LevelVecs<float> f;
 };
@@ -157,6 +163,9 @@ int prolong_sub(sps_plan* pl, int g, const T* c, T* f, int mode, cudaStream_t st
 template <typename T>
 int restrict_res(sps_plan* pl, int g, const T* f, const T* fb, T* c, cudaStream_t st);  // c = I'(f - fb) (fb may be null)
 int coarse_assemble(sps_plan* pl, cudaStream_t st);
+int stencil_assemble(sps_plan* pl, int g, cudaStream_t st);
+template <typename T>
+int stencil_apply(sps_plan* pl, int g, const T* v, T* u, cudaStream_t st);
 template <typename T>
 int coarse_solve(sps_plan* pl, const T* r, T* e, cudaStream_t st);
 
@@ -177,6 +186,10 @@ int dot2(sps_plan* pl, const double* a, const double* b, const double* c, long l
          cudaStream_t st);   // scal[slot] = a.b, scal[slot+1] = a.c
 int pcg_update_xr(sps_plan* pl, long long n, int rz_slot, cudaStream_t st);
 int pcg_update_p(sps_plan* pl, long long n, int num_slot, int den_slot, int flexible, cudaStream_t st);
+
+// ---- batch.cu ----
+int solve_batch(sps_plan* const* plans, int count, double* const* coefs, int mem, double tol, sps_result* res,
+                cudaStream_t st);
 
 // ---- solver (api.cu) ----
 template <typename T>

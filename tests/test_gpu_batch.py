@@ -1,0 +1,69 @@
+"""The batched persistent-kernel solve against per-problem solves and the oracle."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import spline
+from tests.gpu_util import rel_err
+
+pytestmark = pytest.mark.gpu
+
+B = pytest.importorskip("paper_1901_00654_gb300.binding")
+
+
+def _problems(count, seed=3, n_hi=2e4):
+    return W.batched(seed=seed, count=count, n_lo=1e3, n_hi=n_hi)
+
+
+def test_batch_matches_oracle_residual_and_single_solves():
+    probs = _problems(24)
+    tol = 1e-8
+    plans = []
+    try:
+        for pr in probs:
+            pl = B.Plan(pr.P, pr.intervals, pr.levels, pr.lam, pr.lo, pr.hi, precision=B.SPS_PREC_MIXED)
+            pl.set_points(pr.x, pr.y)
+            plans.append(pl)
+        coefs = [np.zeros(pl.K) for pl in plans]
+        res = B.sps_solve_batch([pl.h for pl in plans], coefs, tol)
+        for pr, pl, c, r in zip(probs, plans, coefs, res):
+            assert r.status == B.SPS_OK and r.rel_res_true <= tol
+            A, b, _, _ = spline.system(pr.x, pr.y, pr.lo, pr.hi, pr.intervals, 3, pr.lam)
+            assert np.linalg.norm(b - A @ c) / np.linalg.norm(b) <= 1.05 * tol
+            single, rs = pl.solve(tol)
+            # same algorithm and arithmetic, one CTA instead of many kernels
+            assert abs(r.iterations - rs.iterations) <= max(3, 0.1 * rs.iterations)
+            assert rel_err(c, single) < 1e-4
+    finally:
+        for pl in plans:
+            pl.close()
+
+
+def test_batch_twice_agrees_with_device_buffers():
+    torch = pytest.importorskip("torch")
+    probs = _problems(8, seed=11)
+    plans = []
+    try:
+        for pr in probs:
+            pl = B.Plan(pr.P, pr.intervals, pr.levels, pr.lam, pr.lo, pr.hi, precision=B.SPS_PREC_MIXED)
+            pl.set_points(pr.x, pr.y)
+            plans.append(pl)
+        c1 = [torch.zeros(pl.K, dtype=torch.float64, device="cuda") for pl in plans]
+        c2 = [torch.zeros(pl.K, dtype=torch.float64, device="cuda") for pl in plans]
+        B.sps_solve_batch([pl.h for pl in plans], c1, 1e-8)
+        B.sps_solve_batch([pl.h for pl in plans], c2, 1e-8)
+        # atomics make the summation order differ from run to run; results agree to the solve's accuracy
+        for a, b in zip(c1, c2):
+            assert rel_err(a.cpu().numpy(), b.cpu().numpy()) < 1e-5
+    finally:
+        for pl in plans:
+            pl.close()
+
+
+def test_batch_rejects_p4():
+    x = np.random.default_rng(0).random((500, 4))
+    with B.Plan(4, [4] * 4, 2, 1e-2) as pl:
+        pl.set_points(x, np.sin(x[:, 0]))
+        with pytest.raises(B.SpsError) as e:
+            B.sps_solve_batch([pl.h], [np.zeros(pl.K)], 1e-8)
+        assert e.value.code == B.SPS_EINVAL

@@ -206,9 +206,11 @@ def test_single_level_solve_p5():
     with B.Plan(P, N, 1, 1e-1) as pl:
         pl.set_points(x, y)
         coef, res = pl.solve(1e-10)
-    # the explicit inverse of this ill-conditioned A_1 is not exact: CG finishes the job
+    # the explicit inverse of this ill-conditioned A_1 (cond ~1e15) is not exact:
+    # CG finishes the job; the oracle checks the residual (coefficients of such
+    # a system are not determined to better than cond * eps by any solver)
     assert res.iterations <= 10
-    assert rel_err(coef, mgcg.solve_direct(A, b)) < 1e-6
+    assert np.linalg.norm(b - A @ coef) / np.linalg.norm(b) <= 1.05e-10
 
 
 # ------------------------------------------------------------------ the PR1 workload
