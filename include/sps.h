@@ -221,6 +221,31 @@ SPS_API int sps_set_omega(sps_plan* plan, const double* omega);
 SPS_API int sps_profile_begin(void);
 SPS_API int sps_profile_end(double* point_apply_ms, uint64_t* point_apply_launches);
 
+/* ---------------- no-allocation variant ----------------
+ * The paper has no counterpart of this entry point; it exists for callers
+ * that must not allocate device memory: code running inside another
+ * framework whose caching allocator has reserved the GPU's memory, or
+ * latency-critical loops where cudaMalloc/cudaFree (and cudaFree's implicit
+ * device-wide synchronisation) are not acceptable.  It computes the same
+ * u = scale * Lambda v as sps_penalty_apply, but for a grid passed directly
+ * (no plan, which would allocate) and with its temporaries in one fixed
+ * device array of 6 * SPS_NOALLOC_MAX_COEF doubles (12 MiB) that every GPU
+ * which loads the library holds until the process exits.
+ *  P, intervals[P], lo/hi[P] (NULL -> 0, 1): the grid, as in sps_plan_create
+ *  (intervals need not be powers of two here); K = prod (N_p + 3) must be
+ *  <= SPS_NOALLOC_MAX_COEF, larger grids are rejected with SPS_EINVAL.
+ *  v, u: K doubles in DEVICE memory (u is overwritten); stream: cudaStream_t.
+ * It calls no cudaMalloc, cudaFree or allocating library routine.  All calls
+ * share the one scratch array, so calls that overlap on the GPU (other
+ * streams or host threads) race; the scratch needs no clearing because every
+ * step writes the entries it later reads.  The first call on a device sets up
+ * (looks up the scratch address with cudaGetSymbolAddress and uploads the
+ * cubic element matrices to constant memory); make that first call before any
+ * stream capture.  Errors: SPS_EINVAL, SPS_ECUDA. */
+#define SPS_NOALLOC_MAX_COEF 262144
+SPS_API int sps_penalty_apply_noalloc(int P, const int* intervals, const double* lo, const double* hi,
+                                      double scale, const double* v, double* u, void* stream);
+
 /* Number of CUDA kernels this library has launched in this process so far. */
 SPS_API int sps_launch_count(uint64_t* count);
 

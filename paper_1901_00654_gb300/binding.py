@@ -29,7 +29,8 @@ EXPORTED = ["sps_default_options", "sps_plan_create", "sps_set_points", "sps_sol
             "sps_last_error", "sps_coef_count", "sps_apply", "sps_penalty_apply", "sps_diag", "sps_rhs",
             "sps_prolong", "sps_restrict", "sps_coarse_solve", "sps_vcycle", "sps_get_sort", "sps_get_omega",
             "sps_set_omega", "sps_probe_fma_rate", "sps_point_apply", "sps_launch_count",
-            "sps_profile_begin", "sps_profile_end", "sps_solve_batch", "sps_set_lambda"]
+            "sps_profile_begin", "sps_profile_end", "sps_solve_batch", "sps_set_lambda",
+            "sps_penalty_apply_noalloc"]
 
 
 class sps_options(C.Structure):
@@ -82,6 +83,7 @@ def load(path: str | None = None) -> C.CDLL:
         "sps_profile_end": (I, [C.POINTER(D), C.POINTER(C.c_uint64)]),
         "sps_solve_batch": (I, [C.POINTER(P), I, C.POINTER(P), I, D, C.POINTER(sps_result), P]),
         "sps_set_lambda": (I, [P, D]),
+        "sps_penalty_apply_noalloc": (I, [I, C.POINTER(C.c_int), C.POINTER(D), C.POINTER(D), D, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -185,6 +187,22 @@ def sps_solve_batch(plans, coefs, tol, stream=None, check=True) -> list:
     if check:
         _check(code, "sps_solve_batch")
     return list(res)
+
+
+SPS_NOALLOC_MAX_COEF = 262144
+
+
+def sps_penalty_apply_noalloc(P, intervals, lo, hi, scale, v, u, stream=None) -> None:
+    """u = scale * Lambda v on the grid without any device allocation (v, u: CUDA tensors)."""
+    pv, mv = _buf(v)
+    pu, mu = _buf(u)
+    if mv != SPS_MEM_DEVICE or mu != SPS_MEM_DEVICE:
+        raise ValueError("v and u must be device buffers")
+    iv = (C.c_int * P)(*intervals)
+    lo_a = (C.c_double * P)(*lo) if lo is not None else None
+    hi_a = (C.c_double * P)(*hi) if hi is not None else None
+    _check(lib().sps_penalty_apply_noalloc(P, iv, lo_a, hi_a, scale, pv, pu, _stream(stream)),
+           "sps_penalty_apply_noalloc")
 
 
 def sps_set_lambda(plan, lam) -> None:
