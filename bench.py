@@ -366,6 +366,35 @@ def run_apply_only(args, pr):
     print(json.dumps(out), flush=True)
 
 
+def run_launch_profile(args, pr):
+    """One set-up and one solve of the bench workload, capped at --profile-iters
+    outer iterations: a short run with the same kernel mix per iteration as a
+    timed step, for an ncu launch list (ncu intercepts every launch, so a
+    whole bench run is far too long under it)."""
+    import torch
+
+    from paper_1901_00654_gb300 import binding as B
+    from paper_1901_00654_gb300 import build as libbuild
+    libbuild.build_library()
+    x_d = torch.from_numpy(np.ascontiguousarray(pr.x)).cuda()
+    y_d = torch.from_numpy(np.ascontiguousarray(pr.y)).cuda()
+    prec = B.SPS_PREC_MIXED if pr.precision == "mixed" else B.SPS_PREC_FP64
+    with B.Plan(pr.P, pr.intervals, pr.levels, pr.lam, pr.lo, pr.hi, precision=prec,
+                max_iter=args.profile_iters) as plan:
+        coef = torch.zeros(plan.K, dtype=torch.float64, device="cuda")
+        l0 = B.sps_launch_count()
+        B.sps_profile_begin()
+        t0 = time.perf_counter()
+        plan.set_points(x_d, y_d)
+        _, res = plan.solve(pr.tol, coef, check=False)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        pm, pn = B.sps_profile_end()
+        print(json.dumps({"workload": workload_desc(pr), "iterations": res.iterations, "launches": B.sps_launch_count() - l0,
+                          "wall_ms": wall * 1e3, "point_apply_ms": pm, "point_apply_launches": pn,
+                          "point_apply_share_of_wall": pm / (wall * 1e3)}), flush=True)
+
+
 def run_batched(args):
     """The batched workload: 512 independent problems solved by one persistent
     graph-captured launch (plans resident), against the same problems solved
@@ -468,6 +497,8 @@ def main():
     ap.add_argument("--config", default="scale", choices=["scale", "pr1", "mixed", "batched", "serving"])
     ap.add_argument("--apply-only", action="store_true", help="time the finest-level point operator only")
     ap.add_argument("--reps", type=int, default=10)
+    ap.add_argument("--launch-profile", action="store_true", help="one set-up + capped solve (ncu launch list)")
+    ap.add_argument("--profile-iters", type=int, default=100)
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--batch-tol", type=float, default=1e-8)
     ap.add_argument("--seq-sample", type=int, default=32)
@@ -487,6 +518,8 @@ def main():
     pr = make_problem(args.config, args.n)
     if args.apply_only:
         return run_apply_only(args, pr)
+    if args.launch_profile:
+        return run_launch_profile(args, pr)
     if args.impl == "reference":
         run_reference(args, pr)
     else:

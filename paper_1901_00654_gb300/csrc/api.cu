@@ -94,6 +94,8 @@ void free_vecs(LevelVecs<T>& v) {
 }
 
 void free_points(sps_plan* pl) {
+  if (pl->x32_sorted != pl->x_sorted) cudaFree(pl->x32_sorted);
+  pl->x32_sorted = nullptr;
   cudaFree(pl->x_sorted);
   cudaFree(pl->y_sorted);
   cudaFree(pl->keys);
@@ -268,10 +270,15 @@ int estimate_omega(sps_plan* pl, int g, cudaStream_t st) {
   const int iters = std::max(pl->opt.power_iters, 1);
   for (int it = 0; it < iters; ++it) {
     k_mul<<<blocks, 256, 0, st>>>(y, s, x, K);
-    SPS_TRY(vec_cast_d2f(L.f.alpha, y, K, st));
-    SPS_TRY(apply_level<float>(pl, g, L.f.alpha, L.f.u, st));
-    SPS_TRY(vec_cast_f2d(y, L.f.u, K, st));
-    k_mul<<<blocks, 256, 0, st>>>(y, s, y, K);
+    if (L.st_d) {   // assembled FP64 level: its stencil product is the cheapest apply
+      SPS_TRY(apply_level<double>(pl, g, y, pl->dtmp[6], st));
+      k_mul<<<blocks, 256, 0, st>>>(y, s, pl->dtmp[6], K);
+    } else {
+      SPS_TRY(vec_cast_d2f(L.f.alpha, y, K, st));
+      SPS_TRY(apply_level<float>(pl, g, L.f.alpha, L.f.u, st));
+      SPS_TRY(vec_cast_f2d(y, L.f.u, K, st));
+      k_mul<<<blocks, 256, 0, st>>>(y, s, y, K);
+    }
     SPS_TRY(dot(pl, x, y, K, S_TMP2, st));       // Rayleigh quotient (|x| = 1)
     SPS_TRY(dot(pl, y, y, K, S_TMP, st));
     k_normalize<<<blocks, 256, 0, st>>>(x, y, K, pl->scal, S_TMP);
@@ -646,6 +653,7 @@ int sps_plan_create(sps_plan** out, int P, int q, const int* intervals, const do
       G.lo[p] = pl->lo[p];
       G.inv_h[p] = (double)G.N[p] / (pl->hi[p] - pl->lo[p]);
       G.E[p] = std::min(G.ts, G.N[p]) + Q;
+      G.invE[p] = 1.0f / (float)G.E[p];
     }
     int es = 1;
     for (int p = P - 1; p >= 0; --p) {
@@ -743,6 +751,7 @@ int sps_destroy(sps_plan* pl) {
     cudaFree(L.st_f);
     cudaFree(L.run_begin);
     cudaFree(L.run_cell);
+    cudaFree(L.run_order);
     cudaFree(L.items);
   }
   free_points(pl);
@@ -795,10 +804,12 @@ int sps_set_points(sps_plan* pl, int64_t n, const void* x, const void* y, int dt
     int rc;
     if ((rc = alloc((char**)&pl->x_sorted, (long long)es * P * n)) || (rc = alloc(&pl->y_sorted, n)) ||
         (rc = alloc(&pl->keys, n)) || (rc = alloc(&pl->keys_tmp, n)) || (rc = alloc(&pl->perm, n)) ||
-        (rc = alloc(&pl->perm_tmp, n))) {
+        (rc = alloc(&pl->perm_tmp, n)) ||
+        (dtype == SPS_F64 && (rc = alloc(&pl->x32_sorted, (long long)P * n)))) {
       free_points(pl);
       return rc;
     }
+    if (dtype == SPS_F32) pl->x32_sorted = (float*)pl->x_sorted;
     pl->n_cap = n;
   }
   pl->n = n;

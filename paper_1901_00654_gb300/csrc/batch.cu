@@ -41,7 +41,8 @@ struct BatchLevel {
 struct BatchProblem {
   int P, G, x_f64, nu1, nu2, max_iter;
   long long n;
-  const void* xs;
+  const void* xs;        // sorted coordinates in the input precision (FP64 path)
+  const float* xs32;     // the same rounded to FP32 (FP32 path)
   double lam, tol, ratio, rhs_norm;
   float* ftmp[8];
   double* dtmp[6];
@@ -114,8 +115,8 @@ __device__ void cta_point(const BatchProblem& pb, const BatchLevel& L, const T* 
       T bv[P][4];
 #pragma unroll
       for (int p = 0; p < P; ++p) {
-        const T xp = pb.x_f64 ? T(((const double*)pb.xs)[(long long)p * pb.n + i])
-                              : T(((const float*)pb.xs)[(long long)p * pb.n + i]);
+        const T xp = (sizeof(T) == 4 || !pb.x_f64) ? T(pb.xs32[(long long)p * pb.n + i])
+                                                    : T(((const double*)pb.xs)[(long long)p * pb.n + i]);
         cubic(fma(xp, inv[p], -tsh[p]), bv[p]);
       }
       T s = T(0);
@@ -527,6 +528,7 @@ int solve_batch(sps_plan* const* plans, int count, double* const* coefs, int mem
     b.max_iter = pl->opt.max_iter;
     b.n = pl->n;
     b.xs = pl->x_sorted;
+    b.xs32 = pl->x32_sorted;
     b.lam = pl->lam;
     b.tol = tol;
     b.ratio = pl->opt.replace_ratio > 0 ? pl->opt.replace_ratio : 1e-2;

@@ -309,26 +309,51 @@ __global__ void k_d2f_scaled(const double* __restrict__ a, float* __restrict__ b
 
 // u = A_st v for an assembled level: one thread per row, offsets in the
 // outer loop so that the matrix (offset-major) and v are read coalesced.
-template <typename T>
-__global__ void k_stencil_spmv(const T* __restrict__ A, LevelGeom geom, int S, const T* __restrict__ v,
+// The (2q+1)^P offsets are walked as nested loops restricted to the row's
+// valid range per dimension (no integer division in the loop).
+template <int P, typename T>
+__global__ void k_stencil_spmv(const T* __restrict__ A, LevelGeom geom, const T* __restrict__ v,
                                T* __restrict__ u) {
   const long long K = geom.K;
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < K; k += (long long)gridDim.x * blockDim.x) {
-    int j[MAXP];
-    for (int p = 0; p < geom.P; ++p) j[p] = (int)((k / geom.stride[p]) % geom.J[p]);
+    int lo[P], hi[P];
+    long long rem = k;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      const int j = (int)(rem / geom.stride[p]);
+      rem -= (long long)j * geom.stride[p];
+      lo[p] = max(-Q, -j);
+      hi[p] = min(Q, geom.J[p] - 1 - j);
+    }
     T acc = T(0);
-    for (int s = 0; s < S; ++s) {
-      int ss = s;
-      long long off = 0;
-      bool ok = true;
-      for (int p = geom.P - 1; p >= 0; --p) {
-        const int o = ss % BAND - Q;
-        ss /= BAND;
-        const int jj = j[p] + o;
-        ok = ok && jj >= 0 && jj < geom.J[p];
-        off += (long long)o * geom.stride[p];
+    // odometer over the valid box; s and the v offset advance incrementally
+    int o[P];
+    long long sw[P];
+    sw[P - 1] = 1;
+#pragma unroll
+    for (int p = P - 2; p >= 0; --p) sw[p] = sw[p + 1] * BAND;
+#pragma unroll
+    for (int p = 0; p < P; ++p) o[p] = lo[p];
+    for (;;) {
+      long long s = 0, off = 0;
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        s += (long long)(o[p] + Q) * sw[p];
+        off += (long long)o[p] * geom.stride[p];
       }
-      if (ok) acc = fma(A[(long long)s * K + k], v[k + off], acc);
+      // innermost dimension as a straight loop
+      const long long sK = s * K;
+      for (int oi = lo[P - 1]; oi <= hi[P - 1]; ++oi)
+        acc = fma(A[sK + (long long)(oi - lo[P - 1]) * K + k], v[k + off + (oi - lo[P - 1])], acc);
+      int p = P - 2;
+      for (; p >= 0; --p) {
+        if (o[p] < hi[p]) {
+          ++o[p];
+          break;
+        }
+        o[p] = lo[p];
+      }
+      if (p < 0) break;
     }
     u[k] = acc;
   }
@@ -721,7 +746,14 @@ int stencil_apply(sps_plan* pl, int g, const T* v, T* u, cudaStream_t st) {
   Level& L = pl->lev[g - 1];
   const T* A = nullptr;
   if constexpr (sizeof(T) == 8) A = (const T*)L.st_d; else A = (const T*)L.st_f;
-  k_stencil_spmv<T><<<grid_blocks(L.geom.K, EW_THREADS), EW_THREADS, 0, st>>>(A, L.geom, L.S, v, u);
+  const int blocks = grid_blocks(L.geom.K, EW_THREADS);
+  switch (pl->P) {
+    case 1: k_stencil_spmv<1, T><<<blocks, EW_THREADS, 0, st>>>(A, L.geom, v, u); break;
+    case 2: k_stencil_spmv<2, T><<<blocks, EW_THREADS, 0, st>>>(A, L.geom, v, u); break;
+    case 3: k_stencil_spmv<3, T><<<blocks, EW_THREADS, 0, st>>>(A, L.geom, v, u); break;
+    case 4: k_stencil_spmv<4, T><<<blocks, EW_THREADS, 0, st>>>(A, L.geom, v, u); break;
+    default: k_stencil_spmv<5, T><<<blocks, EW_THREADS, 0, st>>>(A, L.geom, v, u); break;
+  }
   SPS_CHECK_LAUNCH("stencil apply");
   return SPS_OK;
 }

@@ -48,7 +48,8 @@ __device__ __forceinline__ void cubic_basis(T t, T* b) {
 template <int P, typename T, typename CT, int MODE>
 __global__ void __launch_bounds__(POINT_THREADS, 2)
 k_point(const WorkItem* __restrict__ items, const int* __restrict__ run_begin,
-        const unsigned long long* __restrict__ run_cell, const CT* __restrict__ xs, long long n,
+        const unsigned long long* __restrict__ run_cell, const int* __restrict__ run_order,
+        const CT* __restrict__ xs, long long n,
         const double* __restrict__ ys, const T* __restrict__ v, T* __restrict__ u, LevelGeom geom) {
   constexpr int R = P < 3 ? P : 3;            // dimensions held in a lane's registers
   constexpr int NR = ipow4(R);
@@ -76,8 +77,11 @@ k_point(const WorkItem* __restrict__ items, const int* __restrict__ run_begin,
       bool inb = true;
 #pragma unroll
       for (int p = P - 1; p >= 0; --p) {
-        const int m = rem % geom.E[p];
-        rem /= geom.E[p];
+        // rem / E by a float product: (rem + 0.5) / E is at least 1/(2E) away
+        // from an integer, far more than the rounding error for rem < 2^16
+        const int qd = (int)(((float)rem + 0.5f) * geom.invE[p]);
+        const int m = rem - qd * geom.E[p];
+        rem = qd;
         const int j = it.c0[p] + m;
         inb = inb && j < geom.J[p];
         gi += (long long)j * geom.stride[p];
@@ -105,7 +109,10 @@ k_point(const WorkItem* __restrict__ items, const int* __restrict__ run_begin,
 #pragma unroll
   for (int p = 0; p < P; ++p) inv[p] = T(geom.inv_h[p]);
 
-  for (int r = it.run_lo + group; r < it.run_hi; r += ngroups) {
+  // one run per thread when TPP == 1 (runs_per_item == ngroups): which lanes hold one
+  const unsigned has_run_mask = __ballot_sync(0xffffffffu, it.run_lo + group < it.run_hi);
+  for (int rr = it.run_lo + group; rr < it.run_hi; rr += ngroups) {
+    const int r = run_order[rr];
     const int i0 = run_begin[r], i1 = run_begin[r + 1];
     const unsigned long long pc = run_cell[r];
     T tsh[P];
@@ -225,8 +232,34 @@ k_point(const WorkItem* __restrict__ items, const int* __restrict__ run_begin,
         for (int d = 0; d < 4; ++d) accr[d] = fma(w, bv[P - 1][d], accr[d]);
       }
     }
+    bool flushed = false;
+    if (TPP == 1 && NR == 64 && has_run_mask == 0xffffffffu) {
+      // Coarse levels put a whole warp's runs in one cell: reduce the 64 sums
+      // across the warp first (reduce-scatter; lane l ends with the totals of
+      // coefficients 2l and 2l+1) instead of 32-way conflicting atomics.
+      const unsigned long long pc0 = __shfl_sync(0xffffffffu, pc, 0);
+      if (__all_sync(0xffffffffu, pc == pc0)) {
+        const int lane = threadIdx.x & 31;
 #pragma unroll
-    for (int k = 0; k < NR; ++k) atomicAdd(&acc[vidx(k)], accr[k]);
+        for (int step = 0; step < 5; ++step) {
+          const int o = 16 >> step, h = 32 >> step;
+          const bool up = (lane & o) != 0;
+#pragma unroll
+          for (int i = 0; i < h; ++i) {
+            const T send = up ? accr[i] : accr[i + h];
+            const T keep = up ? accr[i + h] : accr[i];
+            accr[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+          }
+        }
+        atomicAdd(&acc[vidx(2 * lane)], accr[0]);
+        atomicAdd(&acc[vidx(2 * lane + 1)], accr[1]);
+        flushed = true;
+      }
+    }
+    if (!flushed) {
+#pragma unroll
+      for (int k = 0; k < NR; ++k) atomicAdd(&acc[vidx(k)], accr[k]);
+    }
   }
   __syncthreads();
 
@@ -238,8 +271,9 @@ k_point(const WorkItem* __restrict__ items, const int* __restrict__ run_begin,
     bool inb = true;
 #pragma unroll
     for (int p = P - 1; p >= 0; --p) {
-      const int m = rem % geom.E[p];
-      rem /= geom.E[p];
+      const int qd = (int)(((float)rem + 0.5f) * geom.invE[p]);
+      const int m = rem - qd * geom.E[p];
+      rem = qd;
       const int j = it.c0[p] + m;
       inb = inb && j < geom.J[p];
       gi += (long long)j * geom.stride[p];
@@ -271,9 +305,9 @@ int launch_point(sps_plan* pl, const Level& L, const T* v, T* u, cudaStream_t st
   }
   const bool timed = MODE == PT_APPLY && g_prof.active && g_prof.used < PROFILE_MAX;
   if (timed) SPS_CUDA(cudaEventRecord(g_prof.ev[2 * g_prof.used], st));
-  k_point<P, T, CT, MODE><<<L.nitems, POINT_THREADS, smem, st>>>(L.items, L.run_begin, L.run_cell,
-                                                       (const CT*)pl->x_sorted, pl->n, pl->y_sorted, v, u,
-                                                       L.geom);
+  const CT* xs = sizeof(CT) == 4 ? (const CT*)pl->x32_sorted : (const CT*)pl->x_sorted;
+  k_point<P, T, CT, MODE><<<L.nitems, POINT_THREADS, smem, st>>>(L.items, L.run_begin, L.run_cell, L.run_order,
+                                                                 xs, pl->n, pl->y_sorted, v, u, L.geom);
   SPS_CHECK_LAUNCH("point operator");
   if (timed) SPS_CUDA(cudaEventRecord(g_prof.ev[2 * g_prof.used++ + 1], st));
   return SPS_OK;
@@ -281,7 +315,7 @@ int launch_point(sps_plan* pl, const Level& L, const T* v, T* u, cudaStream_t st
 
 template <int P, typename T>
 int dispatch_mode(sps_plan* pl, const Level& L, int mode, const T* v, T* u, cudaStream_t st) {
-  if (pl->dtype == SPS_F64) {
+  if (pl->dtype == SPS_F64 && sizeof(T) == 8) {
     if (mode == PT_APPLY) return launch_point<P, T, double, PT_APPLY>(pl, L, v, u, st);
     if (mode == PT_DIAG) return launch_point<P, T, double, PT_DIAG>(pl, L, v, u, st);
     return launch_point<P, T, double, PT_RHS>(pl, L, v, u, st);

@@ -145,11 +145,15 @@ __global__ void k_rs_scatter(const unsigned long long* __restrict__ kin, const u
 template <typename CT>
 __global__ void k_gather(const CT* __restrict__ x, const CT* __restrict__ y,
                          const unsigned int* __restrict__ perm, long long n, int P,
-                         CT* __restrict__ xs, double* __restrict__ ys) {
+                         CT* __restrict__ xs, float* __restrict__ xs32, double* __restrict__ ys) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     long long s = perm[i];
-    for (int p = 0; p < P; ++p) xs[(long long)p * n + i] = x[s * P + p];
+    for (int p = 0; p < P; ++p) {
+      const CT xv = x[s * P + p];
+      xs[(long long)p * n + i] = xv;
+      if (xs32) xs32[(long long)p * n + i] = (float)xv;   // FP32 copy for the FP32 kernels
+    }
     ys[i] = (double)y[s];
   }
 }
@@ -239,6 +243,41 @@ __global__ void k_fill_items(const unsigned int* __restrict__ run_off, const uns
   }
 }
 
+// Order the runs of each work item by length, longest first (bitonic sort of
+// at most 128 runs in shared memory, ties by run index), so that the lanes of
+// a warp walk runs of similar length.
+__global__ void k_sort_item_runs(const WorkItem* __restrict__ items, const int* __restrict__ run_begin,
+                                 int* __restrict__ run_order) {
+  __shared__ long long key[128];
+  const WorkItem it = items[blockIdx.x];
+  const int nr = it.run_hi - it.run_lo;
+  const int t = threadIdx.x;
+  if (t < 128) {
+    if (t < nr) {
+      const int r = it.run_lo + t;
+      const long long len = run_begin[r + 1] - run_begin[r];
+      key[t] = ((128 - len) << 20) | (long long)t;    // ascending key = longest first, then index
+    } else {
+      key[t] = 0x7fffffffffffffffLL;
+    }
+  }
+  __syncthreads();
+  for (int k = 2; k <= 128; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const int l = t ^ j;
+      if (t < 128 && l > t) {
+        const bool asc = (t & k) == 0;
+        const long long a = key[t], b = key[l];
+        if ((a > b) == asc) {
+          key[t] = b;
+          key[l] = a;
+        }
+      }
+      __syncthreads();
+    }
+  if (t < nr) run_order[it.run_lo + t] = it.run_lo + (int)(key[t] & 0xFFFFF);
+}
+
 int ensure_seg(sps_plan* pl, long long need) {
   if (pl->seg_cap >= need) return SPS_OK;
   if (pl->seg_tmp) cudaFree(pl->seg_tmp);
@@ -325,10 +364,10 @@ int gather_points(sps_plan* pl, const void* x_dev, const void* y_dev, int dtype,
   int blocks = grid_blocks(pl->n, 256);
   if (dtype == SPS_F64)
     k_gather<double><<<blocks, 256, 0, st>>>((const double*)x_dev, (const double*)y_dev, pl->perm, pl->n, pl->P,
-                                             (double*)pl->x_sorted, pl->y_sorted);
+                                             (double*)pl->x_sorted, pl->x32_sorted, pl->y_sorted);
   else
     k_gather<float><<<blocks, 256, 0, st>>>((const float*)x_dev, (const float*)y_dev, pl->perm, pl->n, pl->P,
-                                            (float*)pl->x_sorted, pl->y_sorted);
+                                            (float*)pl->x_sorted, nullptr, pl->y_sorted);
   SPS_CHECK_LAUNCH("gather");
   return SPS_OK;
 }
@@ -355,12 +394,15 @@ int build_level_work(sps_plan* pl, int g, cudaStream_t st) {
   if ((int)nruns > L.run_cap) {   // grow only: cudaFree would synchronise the whole device
     cudaFree(L.run_begin);
     cudaFree(L.run_cell);
+    cudaFree(L.run_order);
     L.run_begin = nullptr;
     L.run_cell = nullptr;
+    L.run_order = nullptr;
     L.run_cap = 0;
     const unsigned int cap = nruns + nruns / 4 + 16;
     if (cudaMalloc(&L.run_begin, sizeof(int) * (cap + 1)) != cudaSuccess ||
-        cudaMalloc(&L.run_cell, sizeof(unsigned long long) * cap) != cudaSuccess) {
+        cudaMalloc(&L.run_cell, sizeof(unsigned long long) * cap) != cudaSuccess ||
+        cudaMalloc(&L.run_order, sizeof(int) * cap) != cudaSuccess) {
       set_error("allocation of run lists failed");
       return SPS_ENOMEM;
     }
@@ -398,6 +440,10 @@ int build_level_work(sps_plan* pl, int g, cudaStream_t st) {
   k_fill_items<<<grid_blocks(ntile, 256), 256, 0, st>>>(run_off, item_off, ntile, P * tb, cap, P, tbits, tb,
                                                         L.items);
   SPS_CHECK_LAUNCH("fill items");
+  if (nitems > 0) {
+    k_sort_item_runs<<<nitems, 128, 0, st>>>(L.items, L.run_begin, L.run_order);
+    SPS_CHECK_LAUNCH("sort item runs");
+  }
   return SPS_OK;
 }
 

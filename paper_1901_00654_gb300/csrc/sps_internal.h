@@ -37,6 +37,7 @@ struct LevelGeom {
   double lo[MAXP];
   int ts;               // tile side in level cells (power of two)
   int E[MAXP];          // patch extent per dimension: min(ts, N_p) + q
+  float invE[MAXP];     // 1 / E (patch index division, exact for the sizes used)
   int Es[MAXP];         // patch strides (last dimension fastest)
   int patch;            // prod E
 };
@@ -62,6 +63,7 @@ struct Level {
   // runs: points [run_begin[r], run_begin[r+1]) share one level cell run_cell[r]
   int* run_begin = nullptr;
   unsigned long long* run_cell = nullptr;   // 12 bits per dimension
+  int* run_order = nullptr;                 // runs of each item sorted by length (longest first)
   int nruns = 0, run_cap = 0;
   WorkItem* items = nullptr;
   int nitems = 0, item_cap = 0;
@@ -92,6 +94,7 @@ struct sps_plan {
   long long n = 0, n_cap = 0;
   int dtype = SPS_F64;
   void* x_sorted = nullptr;   // P x n SoA in the input dtype
+  float* x32_sorted = nullptr; // P x n SoA rounded to FP32 (aliases x_sorted for FP32 input)
   double* y_sorted = nullptr;
   unsigned long long* keys = nullptr;
   unsigned int* perm = nullptr;
@@ -144,7 +147,7 @@ void count_launches(unsigned long long k);
 // ---- sort.cu ----
 int compute_keys(sps_plan* pl, const void* x_dev, int dtype, cudaStream_t st);
 int radix_sort(sps_plan* pl, int nbits, cudaStream_t st);
-int gather_points(sps_plan* pl, const void* x_dev, const void* y_dev, int dtype, cudaStream_t st);
+int gather_points(sps_plan* pl, const void* x_dev, const void* y_dev, int dtype, cudaStream_t st);   // also fills x32_sorted
 int build_level_work(sps_plan* pl, int g, cudaStream_t st);
 
 // ---- point_op.cu ----
