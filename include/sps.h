@@ -91,6 +91,9 @@ typedef struct sps_options {
                               cheaper to apply than a point sweep are assembled
                               once in sps_set_points (same matrix A_g); 0: every
                               level matrix free */
+    int    graphs;         /* 1 (default): each PCG iteration after the first is
+                              replayed from a CUDA graph captured once per set-up;
+                              0: launched kernel by kernel */
 } sps_options;
 
 typedef struct sps_result {

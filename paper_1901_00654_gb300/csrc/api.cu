@@ -349,11 +349,53 @@ int check_plan_points(const sps_plan* pl) {
   return SPS_OK;
 }
 
+// ---- one PCG iteration as a CUDA graph -------------------------------------
+// The body of an iteration after the first -- V-cycle, the dot products and
+// direction update of Algorithm 8, then the next operator apply and vector
+// updates, and the copy of the scalars to pinned host memory -- is captured
+// once per set-up and replayed; the host only checks the residual between
+// replays.  Scalar slots are fixed (r'z of the new iteration is copied over the
+// old one inside the body).
+template <typename Body>
+int run_iteration(sps_plan* pl, int which, Body&& body, cudaStream_t st) {
+  sps_plan::IterGraph& gr = pl->graph[which];
+  if (!pl->opt.graphs) {
+    SPS_TRY(body(st));
+    SPS_CUDA(cudaStreamSynchronize(st));
+    return SPS_OK;
+  }
+  const bool prof = profile_active();
+  if (!gr.exec || gr.gen != pl->gen || gr.profiled != prof) {
+    if (gr.exec) cudaGraphExecDestroy(gr.exec);
+    gr.exec = nullptr;
+    if (!pl->cap_stream) SPS_CUDA(cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking));
+    SPS_CUDA(cudaStreamSynchronize(st));
+    const int first = profile_mark();
+    cudaGraph_t g;
+    SPS_CUDA(cudaStreamBeginCapture(pl->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const int rc = body(pl->cap_stream);
+    cudaError_t ce = cudaStreamEndCapture(pl->cap_stream, &g);
+    if (rc != SPS_OK) return rc;
+    if (ce != cudaSuccess) return cuda_fail(ce, "graph capture");
+    ce = cudaGraphInstantiate(&gr.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) return cuda_fail(ce, "graph instantiate");
+    gr.prof_first = first;
+    gr.prof_last = profile_mark();
+    profile_capture_end(gr.prof_first, gr.prof_last);
+    gr.gen = pl->gen;
+    gr.profiled = prof;
+  }
+  SPS_CUDA(cudaGraphLaunch(gr.exec, st));
+  SPS_CUDA(cudaStreamSynchronize(st));
+  if (prof) SPS_TRY(profile_harvest(gr.prof_first, gr.prof_last));
+  return SPS_OK;
+}
+
 int solve_fp64(sps_plan* pl, double tol, sps_result* res, bool warm, cudaStream_t st) {
   const int G = pl->G;
   const long long K = pl->lev[G - 1].geom.K;
   const double nb = pl->rhs_norm;
-  int rz = S_RZ_A, rz_next = S_RZ_B;
   int it = 0;
   int status = SPS_OK;
   double rel = 1.0;
@@ -369,31 +411,46 @@ int solve_fp64(sps_plan* pl, double tol, sps_result* res, bool warm, cudaStream_
     }
     SPS_TRY(vcycle_into<double>(pl, pl->r, pl->z, st));
     SPS_CUDA(cudaMemcpyAsync(pl->p, pl->z, sizeof(double) * K, cudaMemcpyDeviceToDevice, st));
-    SPS_TRY(dot(pl, pl->r, pl->z, K, rz, st));
+    SPS_TRY(dot(pl, pl->r, pl->z, K, S_RZ_A, st));
     SPS_TRY(read_scalars(pl, st));
     rel = std::sqrt(pl->host_scal[S_RR]) / nb;
     return SPS_OK;
   };
+  // v = A p; w = r'z / p'v; alpha += w p; r -= w v (Algorithm 8)
+  auto half_apply = [&](cudaStream_t s) -> int {
+    SPS_TRY(apply_level<double>(pl, G, pl->p, pl->v, s));
+    SPS_TRY(dot(pl, pl->p, pl->v, K, S_PV, s));
+    SPS_TRY(pcg_update_xr(pl, K, S_RZ_A, s));
+    SPS_CUDA(cudaMemcpyAsync(pl->host_scal, pl->scal, sizeof(double) * NSCAL, cudaMemcpyDeviceToHost, s));
+    return SPS_OK;
+  };
+  // z = V(r); beta = r'z / r~'z~; p = z + beta p; then the next half_apply
+  auto body = [&](cudaStream_t s) -> int {
+    SPS_TRY(vcycle_into<double>(pl, pl->r, pl->z, s));
+    SPS_TRY(dot(pl, pl->r, pl->z, K, S_RZ_B, s));
+    SPS_TRY(pcg_update_p(pl, K, S_RZ_B, S_RZ_A, 0, s));
+    SPS_CUDA(cudaMemcpyAsync(pl->scal + S_RZ_A, pl->scal + S_RZ_B, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    return half_apply(s);
+  };
   SPS_CUDA(cudaMemsetAsync(pl->scal, 0, sizeof(double) * NSCAL, st));
   SPS_TRY(restart(warm));
   for (int round = 0; round < 4; ++round) {
+    bool first = true;
     while (rel > tol && it < pl->opt.max_iter) {
-      SPS_TRY(apply_level<double>(pl, G, pl->p, pl->v, st));       // v = A p
+      if (first) {
+        SPS_TRY(half_apply(st));
+        SPS_CUDA(cudaStreamSynchronize(st));
+        first = false;
+      } else {
+        SPS_TRY(run_iteration(pl, 0, body, st));
+      }
       res->fp64_applies++;
-      SPS_TRY(dot(pl, pl->p, pl->v, K, S_PV, st));                  // p'v
-      SPS_TRY(pcg_update_xr(pl, K, rz, st));                        // alpha += w p, r -= w v
-      SPS_TRY(read_scalars(pl, st));
       ++it;
       if (pl->host_scal[S_FLAG] != 0.0) {
         status = SPS_EBREAKDOWN;
         break;
       }
       rel = std::sqrt(pl->host_scal[S_RR]) / nb;
-      if (rel <= tol) break;
-      SPS_TRY(vcycle_into<double>(pl, pl->r, pl->z, st));          // z = V(r)
-      SPS_TRY(dot(pl, pl->r, pl->z, K, rz_next, st));
-      SPS_TRY(pcg_update_p(pl, K, rz_next, rz, 0, st));             // p = z + (r'z / r~'z~) p
-      std::swap(rz, rz_next);
     }
     if (status != SPS_OK) break;
     // true residual in FP64; iterate on if the recursion drifted
@@ -434,25 +491,45 @@ int solve_mixed(sps_plan* pl, double tol, sps_result* res, bool warm, cudaStream
     SPS_CUDA(cudaMemcpyAsync(pl->r, pl->rhs, sizeof(double) * K, cudaMemcpyDeviceToDevice, st));
     SPS_TRY(dot(pl, pl->r, pl->r, K, S_RR, st));
   }
-  auto precondition = [&]() -> int {          // z = V32(r)
-    SPS_TRY(vec_cast_d2f(LG.f.b, pl->r, K, st));
-    SPS_TRY(vcycle_into<float>(pl, LG.f.b, a32, st));
-    return vec_cast_f2d(pl->z, a32, K, st);
+  auto precondition = [&](cudaStream_t s) -> int {          // z = V32(r)
+    SPS_TRY(vec_cast_d2f(LG.f.b, pl->r, K, s));
+    SPS_TRY(vcycle_into<float>(pl, LG.f.b, a32, s));
+    return vec_cast_f2d(pl->z, a32, K, s);
   };
-  SPS_TRY(precondition());
+  // v = A32 p; w = r'z / p'v; alpha += w p; r -= w v
+  auto half_apply = [&](cudaStream_t s) -> int {
+    SPS_TRY(vec_cast_d2f(pl->p32, pl->p, K, s));
+    SPS_TRY(apply_level<float>(pl, G, pl->p32, v32, s));            // FP32 operator
+    SPS_TRY(vec_cast_f2d(pl->v, v32, K, s));
+    SPS_TRY(dot(pl, pl->p, pl->v, K, S_PV, s));
+    SPS_CUDA(cudaMemcpyAsync(pl->rprev, pl->r, sizeof(double) * K, cudaMemcpyDeviceToDevice, s));
+    SPS_TRY(pcg_update_xr(pl, K, S_RZ_A, s));
+    SPS_CUDA(cudaMemcpyAsync(pl->host_scal, pl->scal, sizeof(double) * NSCAL, cudaMemcpyDeviceToHost, s));
+    return SPS_OK;
+  };
+  // z = V32(r); beta = z'(r - r_prev) / r~'z~; p = z + beta p; then half_apply
+  auto body = [&](cudaStream_t s) -> int {
+    SPS_TRY(precondition(s));
+    SPS_TRY(dot2(pl, pl->z, pl->r, pl->rprev, K, S_RZ_B, s));      // z'r, z'r_prev
+    SPS_TRY(pcg_update_p(pl, K, S_RZ_B, S_RZ_A, 1, s));
+    SPS_CUDA(cudaMemcpyAsync(pl->scal + S_RZ_A, pl->scal + S_RZ_B, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    return half_apply(s);
+  };
+  SPS_TRY(precondition(st));
   SPS_CUDA(cudaMemcpyAsync(pl->p, pl->z, sizeof(double) * K, cudaMemcpyDeviceToDevice, st));
   SPS_TRY(dot(pl, pl->r, pl->z, K, S_RZ_A, st));
   SPS_TRY(read_scalars(pl, st));
   rel = std::sqrt(pl->host_scal[S_RR]) / nb;
   rlast = std::sqrt(pl->host_scal[S_RR]);
+  bool restarted = true;   // the next step is a half_apply (after the first V-cycle or a replacement)
   while (rel > tol && it < pl->opt.max_iter) {
-    SPS_TRY(vec_cast_d2f(pl->p32, pl->p, K, st));
-    SPS_TRY(apply_level<float>(pl, G, pl->p32, v32, st));            // v = A p (FP32 operator)
-    SPS_TRY(vec_cast_f2d(pl->v, v32, K, st));
-    SPS_TRY(dot(pl, pl->p, pl->v, K, S_PV, st));
-    SPS_CUDA(cudaMemcpyAsync(pl->rprev, pl->r, sizeof(double) * K, cudaMemcpyDeviceToDevice, st));
-    SPS_TRY(pcg_update_xr(pl, K, S_RZ_A, st));
-    SPS_TRY(read_scalars(pl, st));
+    if (restarted) {
+      SPS_TRY(half_apply(st));
+      SPS_CUDA(cudaStreamSynchronize(st));
+      restarted = false;
+    } else {
+      SPS_TRY(run_iteration(pl, 1, body, st));
+    }
     ++it;
     if (pl->host_scal[S_FLAG] != 0.0) {
       status = SPS_EBREAKDOWN;
@@ -469,11 +546,17 @@ int solve_mixed(sps_plan* pl, double tol, sps_result* res, bool warm, cudaStream
       rel = rn / nb;
       rlast = rn;
       if (rel <= tol) break;
+      // continue with the replaced residual: next V-cycle, beta, direction, apply
+      SPS_TRY(body(st));
+      SPS_CUDA(cudaStreamSynchronize(st));
+      ++it;
+      if (pl->host_scal[S_FLAG] != 0.0) {
+        status = SPS_EBREAKDOWN;
+        break;
+      }
+      rn = std::sqrt(pl->host_scal[S_RR]);
+      rel = rn / nb;
     }
-    SPS_TRY(precondition());
-    SPS_TRY(dot2(pl, pl->z, pl->r, pl->rprev, K, S_RZ_B, st));      // z'r, z'r_prev
-    SPS_TRY(pcg_update_p(pl, K, S_RZ_B, S_RZ_A, 1, st));            // beta = z'(r - r_prev) / r~'z~
-    SPS_CUDA(cudaMemcpyAsync(pl->scal + S_RZ_A, pl->scal + S_RZ_B, sizeof(double), cudaMemcpyDeviceToDevice, st));
   }
   res->iterations = it;
   res->rel_res = rel;
@@ -560,6 +643,7 @@ void sps_default_options(sps_options* opt) {
   opt->tile = 0;
   opt->replace_ratio = 1e-2;
   opt->hybrid = 1;
+  opt->graphs = 1;
 }
 
 const char* sps_last_error(void) { return g_last_error.c_str(); }
@@ -737,6 +821,7 @@ int sps_set_lambda(sps_plan* pl, double lambda) {
   }
   pl->lam = lambda;
   pl->have_points = false;   // the diagonals and the coarse matrix depend on lambda
+  ++pl->gen;
   return SPS_OK;
 }
 
@@ -777,6 +862,9 @@ int sps_destroy(sps_plan* pl) {
   cudaFree(pl->sort_hist);
   cudaFree(pl->seg_tmp);
   if (pl->host_scal) cudaFreeHost(pl->host_scal);
+  for (auto& gr : pl->graph)
+    if (gr.exec) cudaGraphExecDestroy(gr.exec);
+  if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
   delete pl;
   return SPS_OK;
 }
@@ -863,6 +951,7 @@ int sps_set_points(sps_plan* pl, int64_t n, const void* x, const void* y, int dt
   SPS_CUDA(cudaStreamSynchronize(st));
   SPS_CUDA(cudaGetLastError());
   pl->have_points = true;
+  ++pl->gen;
   return SPS_OK;
 }
 
@@ -1137,6 +1226,7 @@ int sps_set_omega(sps_plan* pl, const double* omega) {
       return SPS_EINVAL;
     }
   for (int g = 0; g < pl->G; ++g) pl->lev[g].omega = omega[g];
+  ++pl->gen;
   return SPS_OK;
 }
 

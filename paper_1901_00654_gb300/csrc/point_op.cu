@@ -24,6 +24,8 @@
 //    neighbouring tiles overlap in q layers of coefficients.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "sps_internal.h"
 
 namespace sps {
@@ -287,6 +289,9 @@ struct ProfileState {
   bool active = false;
   int used = 0;
   std::vector<cudaEvent_t> ev;   // pairs
+  std::vector<char> in_graph;    // pair recorded by a graph node (harvested per replay)
+  double harvest_ms = 0.0;
+  long long harvest_cnt = 0;
 };
 ProfileState g_prof;
 constexpr int PROFILE_MAX = 8192;
@@ -348,23 +353,51 @@ int profile_begin() {
   if (g_prof.ev.empty()) {
     g_prof.ev.resize(2 * PROFILE_MAX);
     for (auto& e : g_prof.ev) SPS_CUDA(cudaEventCreate(&e));
+    g_prof.in_graph.assign(PROFILE_MAX, 0);
   }
   g_prof.used = 0;
+  std::fill(g_prof.in_graph.begin(), g_prof.in_graph.end(), 0);
+  g_prof.harvest_ms = 0.0;
+  g_prof.harvest_cnt = 0;
   g_prof.active = true;
+  return SPS_OK;
+}
+
+bool profile_active() { return g_prof.active; }
+int profile_mark() { return g_prof.used; }
+
+// Pairs [first, last) were recorded into a graph being captured: they are
+// timed per replay by profile_harvest, not at profile_end.
+void profile_capture_end(int first, int last) {
+  for (int i = first; i < last && i < PROFILE_MAX; ++i) g_prof.in_graph[i] = 1;
+}
+
+// After a replay of a graph holding pairs [first, last) has completed.
+int profile_harvest(int first, int last) {
+  if (!g_prof.active) return SPS_OK;
+  for (int i = first; i < last; ++i) {
+    float t = 0.0f;
+    SPS_CUDA(cudaEventElapsedTime(&t, g_prof.ev[2 * i], g_prof.ev[2 * i + 1]));
+    g_prof.harvest_ms += t;
+    ++g_prof.harvest_cnt;
+  }
   return SPS_OK;
 }
 
 int profile_end(double* ms, unsigned long long* launches) {
   g_prof.active = false;
-  double tot = 0.0;
+  double tot = g_prof.harvest_ms;
+  unsigned long long cnt = (unsigned long long)g_prof.harvest_cnt;
   for (int i = 0; i < g_prof.used; ++i) {
+    if (g_prof.in_graph[i]) continue;
     SPS_CUDA(cudaEventSynchronize(g_prof.ev[2 * i + 1]));
     float t = 0.0f;
     SPS_CUDA(cudaEventElapsedTime(&t, g_prof.ev[2 * i], g_prof.ev[2 * i + 1]));
     tot += t;
+    ++cnt;
   }
   *ms = tot;
-  *launches = (unsigned long long)g_prof.used;
+  *launches = cnt;
   return SPS_OK;
 }
 

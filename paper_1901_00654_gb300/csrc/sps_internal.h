@@ -124,6 +124,17 @@ struct sps_plan {
   unsigned int* red_count = nullptr;
   double* host_scal = nullptr;    // pinned mirror of scal
   bool have_points = false;
+  // CUDA graph of one PCG iteration (V-cycle, vector updates, apply), per
+  // precision; rebuilt when `gen` (bumped by set_points/set_omega/set_lambda)
+  // or the profiling state changes
+  struct IterGraph {
+    cudaGraphExec_t exec = nullptr;
+    unsigned gen = ~0u;
+    bool profiled = false;
+    int prof_first = 0, prof_last = 0;
+  } graph[2];
+  unsigned gen = 0;
+  cudaStream_t cap_stream = nullptr;
 };
 
 namespace sps {
@@ -156,6 +167,10 @@ template <typename T>
 int point_op(sps_plan* pl, int g, int mode, const T* v, T* u, cudaStream_t st);
 int profile_begin();
 int profile_end(double* ms, unsigned long long* launches);
+bool profile_active();
+int profile_mark();
+void profile_capture_end(int first, int last);
+int profile_harvest(int first, int last);
 
 // ---- grid_ops.cu ----
 template <typename T>

@@ -313,3 +313,21 @@ def test_null_space_recovery_gpu():
     grids = np.meshgrid(*[spline.greville(lo[p], hi[p], intervals[p], 3) for p in range(P)], indexing="ij")
     ref = c[0] + sum(c[p + 1] * grids[p] for p in range(P))
     assert rel_err(coef, ref.ravel()) < 1e-9
+
+
+@pytest.mark.parametrize("prec", [B.SPS_PREC_FP64, B.SPS_PREC_MIXED])
+def test_graph_replay_matches_kernel_by_kernel(prec):
+    """The CUDA-graph replay of an iteration and the kernel-by-kernel loop run
+    the same arithmetic: same iteration count, same coefficients up to the
+    atomics' summation order."""
+    x, y, lo, hi = random_problem(3, [16, 16, 8], 20000, seed=31)
+    out = []
+    for graphs in (0, 1):
+        with B.Plan(3, [16, 16, 8], 4, 1e-3, lo, hi, precision=prec, graphs=graphs) as pl:
+            pl.set_points(x, y)
+            coef, res = pl.solve(1e-10)
+            coef2, res2 = pl.solve(1e-10)        # second solve replays the cached graph
+            out.append((coef, res.iterations, coef2, res2.iterations))
+    (c0, i0, _, _), (c1, i1, c1b, i1b) = out
+    assert abs(i0 - i1) <= 1 and i1 == i1b
+    assert rel_err(c1, c0) < 1e-6 and rel_err(c1b, c1) < 1e-6
