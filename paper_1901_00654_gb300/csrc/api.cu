@@ -372,9 +372,13 @@ int run_iteration(sps_plan* pl, int which, Body&& body, cudaStream_t st) {
     SPS_CUDA(cudaStreamSynchronize(st));
     const int first = profile_mark();
     cudaGraph_t g;
+    const unsigned long long l0 = g_launches.load();
     SPS_CUDA(cudaStreamBeginCapture(pl->cap_stream, cudaStreamCaptureModeThreadLocal));
     const int rc = body(pl->cap_stream);
     cudaError_t ce = cudaStreamEndCapture(pl->cap_stream, &g);
+    // captured kernels run at each replay, not now: count them per replay
+    gr.nlaunch = g_launches.load() - l0;
+    g_launches.fetch_sub(gr.nlaunch);
     if (rc != SPS_OK) return rc;
     if (ce != cudaSuccess) return cuda_fail(ce, "graph capture");
     ce = cudaGraphInstantiate(&gr.exec, g, 0);
@@ -387,6 +391,7 @@ int run_iteration(sps_plan* pl, int which, Body&& body, cudaStream_t st) {
     gr.profiled = prof;
   }
   SPS_CUDA(cudaGraphLaunch(gr.exec, st));
+  count_launches(gr.nlaunch);
   SPS_CUDA(cudaStreamSynchronize(st));
   if (prof) SPS_TRY(profile_harvest(gr.prof_first, gr.prof_last));
   return SPS_OK;
@@ -834,6 +839,7 @@ int sps_destroy(sps_plan* pl) {
     cudaFree(L.diag);
     cudaFree(L.st_d);
     cudaFree(L.st_f);
+    cudaFree(L.pre);
     cudaFree(L.run_begin);
     cudaFree(L.run_cell);
     cudaFree(L.run_order);
@@ -943,6 +949,22 @@ int sps_set_points(sps_plan* pl, int64_t n, const void* x, const void* y, int dt
   pl->rhs_norm = std::sqrt(pl->host_scal[S_TMP]);
   SPS_TRY(coarse_assemble(pl, st));
   SPS_TRY(assemble_coarse_levels(pl, st));
+  // FP64 mode: basis values of the points on every matrix-free level (>= 2)
+  if (pl->opt.precision == SPS_PREC_FP64) {
+    for (int g = 2; g <= G; ++g) {
+      Level& L = pl->lev[g - 1];
+      if (L.st_d) continue;
+      const long long need = pl->n * 4LL * P;
+      if (L.pre_cap < need) {
+        cudaFree(L.pre);
+        L.pre = nullptr;
+        L.pre_cap = 0;
+        SPS_TRY(alloc(&L.pre, need));
+        L.pre_cap = need;
+      }
+      SPS_TRY(basis_precompute(pl, g, st));
+    }
+  }
   for (int g = 2; g <= G; ++g) {
     if (pl->opt.omega > 0.0) pl->lev[g - 1].omega = pl->opt.omega;
     else SPS_TRY(estimate_omega(pl, g, st));

@@ -307,15 +307,22 @@ __global__ void k_d2f_scaled(const double* __restrict__ a, float* __restrict__ b
     b[i] = (float)a[i];
 }
 
-// u = A_st v for an assembled level: one thread per row, offsets in the
-// outer loop so that the matrix (offset-major) and v are read coalesced.
-// The (2q+1)^P offsets are walked as nested loops restricted to the row's
-// valid range per dimension (no integer division in the loop).
+// u = A_st v for an assembled level.  A block is 32 consecutive rows x
+// SPMV_Y offset groups: lane x owns row k (so the offset-major matrix and v
+// are read coalesced), row y of the block takes every SPMV_Y-th combination of
+// the leading P-1 offsets and walks the last offset as a straight loop; the
+// SPMV_Y partial sums of a row are added in shared memory.  Offsets outside the
+// grid are skipped by range, not by division.
+constexpr int SPMV_Y = 8;
+
 template <int P, typename T>
-__global__ void k_stencil_spmv(const T* __restrict__ A, LevelGeom geom, const T* __restrict__ v,
-                               T* __restrict__ u) {
+__global__ void __launch_bounds__(32 * SPMV_Y) k_stencil_spmv(const T* __restrict__ A, LevelGeom geom,
+                                                              const T* __restrict__ v, T* __restrict__ u) {
+  __shared__ T part[SPMV_Y][33];
   const long long K = geom.K;
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < K; k += (long long)gridDim.x * blockDim.x) {
+  const long long k = (long long)blockIdx.x * 32 + threadIdx.x;
+  T acc = T(0);
+  if (k < K) {
     int lo[P], hi[P];
     long long rem = k;
 #pragma unroll
@@ -325,37 +332,44 @@ __global__ void k_stencil_spmv(const T* __restrict__ A, LevelGeom geom, const T*
       lo[p] = max(-Q, -j);
       hi[p] = min(Q, geom.J[p] - 1 - j);
     }
-    T acc = T(0);
-    // odometer over the valid box; s and the v offset advance incrementally
-    int o[P];
-    long long sw[P];
-    sw[P - 1] = 1;
-#pragma unroll
-    for (int p = P - 2; p >= 0; --p) sw[p] = sw[p + 1] * BAND;
-#pragma unroll
-    for (int p = 0; p < P; ++p) o[p] = lo[p];
-    for (;;) {
+    constexpr int NOUT = P == 1 ? 1 : (P == 2 ? BAND : (P == 3 ? BAND * BAND : (P == 4 ? BAND * BAND * BAND
+                                                                                      : BAND * BAND * BAND * BAND)));
+    for (int c = threadIdx.y; c < NOUT; c += SPMV_Y) {
+      // decode the leading offsets of combination c (division by the constant 7)
+      int cc = c;
       long long s = 0, off = 0;
+      bool ok = true;
 #pragma unroll
-      for (int p = 0; p < P; ++p) {
-        s += (long long)(o[p] + Q) * sw[p];
-        off += (long long)o[p] * geom.stride[p];
+      for (int p = P - 2; p >= 0; --p) {
+        const int o = cc % BAND - Q;
+        cc /= BAND;
+        ok = ok && o >= lo[p] && o <= hi[p];
+        off += (long long)o * geom.stride[p];
       }
-      // innermost dimension as a straight loop
-      const long long sK = s * K;
-      for (int oi = lo[P - 1]; oi <= hi[P - 1]; ++oi)
-        acc = fma(A[sK + (long long)(oi - lo[P - 1]) * K + k], v[k + off + (oi - lo[P - 1])], acc);
-      int p = P - 2;
-      for (; p >= 0; --p) {
-        if (o[p] < hi[p]) {
-          ++o[p];
-          break;
+      if (!ok) continue;
+      long long sw = BAND;
+      s = 0;
+      {
+        int c2 = c;
+#pragma unroll
+        for (int p = P - 2; p >= 0; --p) {
+          s += (long long)(c2 % BAND) * sw;
+          c2 /= BAND;
+          sw *= BAND;
         }
-        o[p] = lo[p];
       }
-      if (p < 0) break;
+      // s: index of (leading offsets, last offset = -q); walk the last offset
+      for (int oi = lo[P - 1]; oi <= hi[P - 1]; ++oi)
+        acc = fma(A[(s + oi + Q) * K + k], v[k + off + oi], acc);
     }
-    u[k] = acc;
+  }
+  part[threadIdx.y][threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.y == 0 && k < K) {
+    T t = T(0);
+#pragma unroll
+    for (int y = 0; y < SPMV_Y; ++y) t += part[y][threadIdx.x];
+    u[k] = t;
   }
 }
 
@@ -746,13 +760,14 @@ int stencil_apply(sps_plan* pl, int g, const T* v, T* u, cudaStream_t st) {
   Level& L = pl->lev[g - 1];
   const T* A = nullptr;
   if constexpr (sizeof(T) == 8) A = (const T*)L.st_d; else A = (const T*)L.st_f;
-  const int blocks = grid_blocks(L.geom.K, EW_THREADS);
+  const int blocks = (int)((L.geom.K + 31) / 32);
+  const dim3 tb(32, SPMV_Y);
   switch (pl->P) {
-    case 1: k_stencil_spmv<1, T><<<blocks, EW_THREADS, 0, st>>>(A, L.geom, v, u); break;
-    case 2: k_stencil_spmv<2, T><<<blocks, EW_THREADS, 0, st>>>(A, L.geom, v, u); break;
-    case 3: k_stencil_spmv<3, T><<<blocks, EW_THREADS, 0, st>>>(A, L.geom, v, u); break;
-    case 4: k_stencil_spmv<4, T><<<blocks, EW_THREADS, 0, st>>>(A, L.geom, v, u); break;
-    default: k_stencil_spmv<5, T><<<blocks, EW_THREADS, 0, st>>>(A, L.geom, v, u); break;
+    case 1: k_stencil_spmv<1, T><<<blocks, tb, 0, st>>>(A, L.geom, v, u); break;
+    case 2: k_stencil_spmv<2, T><<<blocks, tb, 0, st>>>(A, L.geom, v, u); break;
+    case 3: k_stencil_spmv<3, T><<<blocks, tb, 0, st>>>(A, L.geom, v, u); break;
+    case 4: k_stencil_spmv<4, T><<<blocks, tb, 0, st>>>(A, L.geom, v, u); break;
+    default: k_stencil_spmv<5, T><<<blocks, tb, 0, st>>>(A, L.geom, v, u); break;
   }
   SPS_CHECK_LAUNCH("stencil apply");
   return SPS_OK;

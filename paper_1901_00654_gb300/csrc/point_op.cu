@@ -47,13 +47,22 @@ __device__ __forceinline__ void cubic_basis(T t, T* b) {
   b[3] = t2 * (t * T(1.0 / 6.0));
 }
 
-template <int P, typename T, typename CT, int MODE>
+// PRE (FP64 only): the 4P basis values of every point on this level were
+// computed once at set-up and are read from `pre` ([point][dimension][m])
+// instead of being re-evaluated from the coordinates in every sweep.  On
+// GB300 an FP64 operation costs about as much as moving 40 bytes from HBM, so
+// streaming 8*4P bytes per point is cheaper than the 12P FP64 operations.
+// RR: dimensions held in a lane's registers (0 = min(P, 3)); the FP32
+// kernel for P = 3 uses RR = 2, i.e. four lanes per run with 16 coefficients
+// each, for four times the resident warps of the one-lane layout.
+template <int P, typename T, typename CT, int MODE, bool PRE = false, int RR = 0>
 __global__ void __launch_bounds__(POINT_THREADS, 2)
 k_point(const WorkItem* __restrict__ items, const int* __restrict__ run_begin,
         const unsigned long long* __restrict__ run_cell, const int* __restrict__ run_order,
         const CT* __restrict__ xs, long long n,
-        const double* __restrict__ ys, const T* __restrict__ v, T* __restrict__ u, LevelGeom geom) {
-  constexpr int R = P < 3 ? P : 3;            // dimensions held in a lane's registers
+        const double* __restrict__ ys, const T* __restrict__ v, T* __restrict__ u, LevelGeom geom,
+        const double* __restrict__ pre = nullptr) {
+  constexpr int R = RR > 0 ? RR : (P < 3 ? P : 3);   // dimensions held in a lane's registers
   constexpr int NR = ipow4(R);
   constexpr int F = P - R;                    // leading dimensions fixed per lane
   constexpr int TPP = ipow4(F);               // lanes per run
@@ -68,9 +77,11 @@ k_point(const WorkItem* __restrict__ items, const int* __restrict__ run_begin,
   const WorkItem it = items[blockIdx.x];
   const int pbeg = run_begin[it.run_lo];
   const int npts = run_begin[it.run_hi] - pbeg;
+  if (!PRE) {
 #pragma unroll
-  for (int p = 0; p < P; ++p)
-    for (int e = threadIdx.x; e < npts; e += blockDim.x) xsh[p * npts + e] = xs[(long long)p * n + pbeg + e];
+    for (int p = 0; p < P; ++p)
+      for (int e = threadIdx.x; e < npts; e += blockDim.x) xsh[p * npts + e] = xs[(long long)p * n + pbeg + e];
+  }
   for (int e = threadIdx.x; e < geom.patch; e += blockDim.x) {
     acc[e] = T(0);
     if (MODE == PT_APPLY) {
@@ -145,14 +156,26 @@ k_point(const WorkItem* __restrict__ items, const int* __restrict__ run_begin,
 
     for (int i = i0; i < i1; ++i) {
       T bv[P][4];
+      if (PRE) {
+        const double2* q = reinterpret_cast<const double2*>(pre + (long long)i * (4 * P));
 #pragma unroll
-      for (int p = 0; p < P; ++p) {
-        const T xp = T(xsh[p * npts + (i - pbeg)]);
-        const T t = fma(xp, inv[p], -tsh[p]);
-        cubic_basis(t, bv[p]);
-        if (MODE == PT_DIAG) {
+        for (int p = 0; p < P; ++p) {
+          const double2 a = __ldg(q + 2 * p), b = __ldg(q + 2 * p + 1);
+          bv[p][0] = T(a.x);
+          bv[p][1] = T(a.y);
+          bv[p][2] = T(b.x);
+          bv[p][3] = T(b.y);
+        }
+      } else {
 #pragma unroll
-          for (int m = 0; m < 4; ++m) bv[p][m] *= bv[p][m];
+        for (int p = 0; p < P; ++p) {
+          const T xp = T(xsh[p * npts + (i - pbeg)]);
+          const T t = fma(xp, inv[p], -tsh[p]);
+          cubic_basis(t, bv[p]);
+          if (MODE == PT_DIAG) {
+#pragma unroll
+            for (int m = 0; m < 4; ++m) bv[p][m] *= bv[p][m];
+          }
         }
       }
       T fixw = T(1);
@@ -284,6 +307,16 @@ k_point(const WorkItem* __restrict__ items, const int* __restrict__ run_begin,
   }
 }
 
+// Event records of the profile: inside a stream capture an ordinary
+// cudaEventRecord only marks a dependency, so the record is captured as an
+// external event-record node, which replays of the graph then record.
+inline cudaError_t record_event(cudaEvent_t e, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(st, &cs);
+  if (cs == cudaStreamCaptureStatusActive) return cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+  return cudaEventRecord(e, st);
+}
+
 // Event pool for sps_profile_begin / sps_profile_end.
 struct ProfileState {
   bool active = false;
@@ -309,12 +342,39 @@ int launch_point(sps_plan* pl, const Level& L, const T* v, T* u, cudaStream_t st
     attr_set = true;
   }
   const bool timed = MODE == PT_APPLY && g_prof.active && g_prof.used < PROFILE_MAX;
-  if (timed) SPS_CUDA(cudaEventRecord(g_prof.ev[2 * g_prof.used], st));
+  if (timed) SPS_CUDA(record_event(g_prof.ev[2 * g_prof.used], st));
   const CT* xs = sizeof(CT) == 4 ? (const CT*)pl->x32_sorted : (const CT*)pl->x_sorted;
-  k_point<P, T, CT, MODE><<<L.nitems, POINT_THREADS, smem, st>>>(L.items, L.run_begin, L.run_cell, L.run_order,
-                                                                 xs, pl->n, pl->y_sorted, v, u, L.geom);
+  if constexpr (sizeof(T) == 8 && MODE == PT_APPLY) {
+    if (L.pre) {
+      static bool attr_pre = false;
+      if (!attr_pre) {
+        SPS_CUDA(cudaFuncSetAttribute(k_point<P, T, CT, MODE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      160 * 1024));
+        attr_pre = true;
+      }
+      const size_t smem_pre = (size_t)2 * L.geom.patch * sizeof(T) + 16;
+      k_point<P, T, CT, MODE, true><<<L.nitems, POINT_THREADS, smem_pre, st>>>(
+          L.items, L.run_begin, L.run_cell, L.run_order, xs, pl->n, pl->y_sorted, v, u, L.geom, L.pre);
+      SPS_CHECK_LAUNCH("point operator");
+      if (timed) SPS_CUDA(record_event(g_prof.ev[2 * g_prof.used++ + 1], st));
+      return SPS_OK;
+    }
+  }
+  if constexpr (sizeof(T) == 4 && P == 3) {
+    static bool attr_r2 = false;
+    if (!attr_r2) {
+      SPS_CUDA(cudaFuncSetAttribute(k_point<P, T, CT, MODE, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    160 * 1024));
+      attr_r2 = true;
+    }
+    k_point<P, T, CT, MODE, false, 2><<<L.nitems, POINT_THREADS, smem, st>>>(
+        L.items, L.run_begin, L.run_cell, L.run_order, xs, pl->n, pl->y_sorted, v, u, L.geom);
+  } else {
+    k_point<P, T, CT, MODE><<<L.nitems, POINT_THREADS, smem, st>>>(L.items, L.run_begin, L.run_cell, L.run_order,
+                                                                   xs, pl->n, pl->y_sorted, v, u, L.geom);
+  }
   SPS_CHECK_LAUNCH("point operator");
-  if (timed) SPS_CUDA(cudaEventRecord(g_prof.ev[2 * g_prof.used++ + 1], st));
+  if (timed) SPS_CUDA(record_event(g_prof.ev[2 * g_prof.used++ + 1], st));
   return SPS_OK;
 }
 
@@ -341,6 +401,62 @@ int point_op(sps_plan* pl, int g, int mode, const T* v, T* u, cudaStream_t st) {
     case 3: return dispatch_mode<3, T>(pl, L, mode, v, u, st);
     case 4: return dispatch_mode<4, T>(pl, L, mode, v, u, st);
     case 5: return dispatch_mode<5, T>(pl, L, mode, v, u, st);
+  }
+  set_error("unsupported dimension");
+  return SPS_EINVAL;
+}
+
+namespace {
+
+// The 4P basis values of every point on level g (one thread per run).
+template <int P, typename CT>
+__global__ void k_basis_pre(const int* __restrict__ run_begin, const unsigned long long* __restrict__ run_cell,
+                            int nruns, const CT* __restrict__ xs, long long n, LevelGeom geom,
+                            double* __restrict__ pre) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nruns; r += gridDim.x * blockDim.x) {
+    const unsigned long long pc = run_cell[r];
+    double tsh[P], inv[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      const int c = (int)((pc >> (12 * p)) & 0xFFFull);
+      inv[p] = geom.inv_h[p];
+      tsh[p] = geom.lo[p] * geom.inv_h[p] + (double)c;
+    }
+    for (int i = run_begin[r]; i < run_begin[r + 1]; ++i) {
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        double b[4];
+        cubic_basis(fma((double)xs[(long long)p * n + i], inv[p], -tsh[p]), b);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) pre[(long long)i * (4 * P) + 4 * p + m] = b[m];
+      }
+    }
+  }
+}
+
+template <int P>
+int basis_pre_launch(sps_plan* pl, const Level& L, cudaStream_t st) {
+  const int blocks = grid_blocks(L.nruns, 128);
+  if (pl->dtype == SPS_F64)
+    k_basis_pre<P, double><<<blocks, 128, 0, st>>>(L.run_begin, L.run_cell, L.nruns, (const double*)pl->x_sorted,
+                                                   pl->n, L.geom, L.pre);
+  else
+    k_basis_pre<P, float><<<blocks, 128, 0, st>>>(L.run_begin, L.run_cell, L.nruns, pl->x32_sorted, pl->n,
+                                                  L.geom, L.pre);
+  SPS_CHECK_LAUNCH("basis precompute");
+  return SPS_OK;
+}
+
+}  // namespace
+
+int basis_precompute(sps_plan* pl, int g, cudaStream_t st) {
+  const Level& L = pl->lev[g - 1];
+  switch (pl->P) {
+    case 1: return basis_pre_launch<1>(pl, L, st);
+    case 2: return basis_pre_launch<2>(pl, L, st);
+    case 3: return basis_pre_launch<3>(pl, L, st);
+    case 4: return basis_pre_launch<4>(pl, L, st);
+    case 5: return basis_pre_launch<5>(pl, L, st);
   }
   set_error("unsupported dimension");
   return SPS_EINVAL;

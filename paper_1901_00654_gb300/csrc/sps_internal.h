@@ -75,6 +75,9 @@ struct Level {
   int S = 0;
   double* st_d = nullptr;
   float* st_f = nullptr;
+  // FP64 matrix-free levels: basis values of every point, [point][dim][m]
+  double* pre = nullptr;
+  long long pre_cap = 0;
   LevelVecs<double> d;
   LevelVecs<float> f;
 };
@@ -132,6 +135,7 @@ struct sps_plan {
     unsigned gen = ~0u;
     bool profiled = false;
     int prof_first = 0, prof_last = 0;
+    unsigned long long nlaunch = 0;   // kernels per replay
   } graph[2];
   unsigned gen = 0;
   cudaStream_t cap_stream = nullptr;
@@ -165,6 +169,7 @@ int build_level_work(sps_plan* pl, int g, cudaStream_t st);
 enum PointMode { PT_APPLY = 0, PT_DIAG = 1, PT_RHS = 2 };
 template <typename T>
 int point_op(sps_plan* pl, int g, int mode, const T* v, T* u, cudaStream_t st);
+int basis_precompute(sps_plan* pl, int g, cudaStream_t st);
 int profile_begin();
 int profile_end(double* ms, unsigned long long* launches);
 bool profile_active();
