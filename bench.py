@@ -395,6 +395,44 @@ def run_launch_profile(args, pr):
                           "point_apply_share_of_wall": pm / (wall * 1e3)}), flush=True)
 
 
+def run_paper(args):
+    """Section 4 of the paper on the GPU: n = 1e5 sigmoid data, plain CG
+    against MGCG -- P = 1..4 on G = 5 grids (Table 2) and P = 2 on
+    G = 4..7 (Fig. 2).  lambda and the tolerance are not stated in the paper;
+    lambda = 0.1 (at which kappa(A) for P = 2, G = 5 is close to the printed
+    1933) and rel.res 1e-6 are used."""
+    import torch
+
+    from paper_1901_00654_gb300 import binding as B
+    from paper_1901_00654_gb300 import build as libbuild
+    libbuild.build_library()
+    lam, tol = 0.1, 1e-6
+    paper = {1: (22, 2), 2: (73, 4), 3: (367, 14), 4: (747, 19)}   # Table 2 iterations (CG, MGCG_JAC)
+
+    def run(P, G):
+        x, y = W.paper_sigmoid(5, 100_000, P)
+        out = {}
+        for name, pc in (("cg", 0), ("mgcg", 1)):
+            with B.Plan(P, [2 ** G] * P, G, lam, precondition=pc, max_iter=50000) as pl:
+                pl.set_points(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda())
+                coef = torch.zeros(pl.K, dtype=torch.float64, device="cuda")
+                pl.solve(tol, coef, check=False)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                _, res = pl.solve(tol, coef, check=False)
+                torch.cuda.synchronize()
+                out[name] = {"iterations": res.iterations, "solve_ms": (time.perf_counter() - t0) * 1e3,
+                             "status": res.status}
+        return out
+
+    table2 = {P: run(P, 5) for P in (1, 2, 3, 4)}
+    fig2 = {G: run(2, G) for G in (4, 5, 6, 7)}
+    line = {"workload": "paper Section 4: n=1e5 sigmoid data, lambda=%g, rel.res %g, FP64" % (lam, tol),
+            "table2_gpu": table2, "fig2_gpu_P2": fig2,
+            "table2_paper_iterations_cg_mgcg": paper}
+    print(json.dumps(line), flush=True)
+
+
 def run_batched(args):
     """The batched workload: 512 independent problems solved by one persistent
     graph-captured launch (plans resident), against the same problems solved
@@ -427,6 +465,7 @@ def run_batched(args):
         times.append(time.perf_counter() - t0)
     bt = statistics.median(times)
     its = [r.iterations for r in res]
+    cta_ms = sorted((r.solve_ms for r in res), reverse=True)
     ok = sum(r.status == B.SPS_OK for r in res)
     # sequential plain FP64 on a sample of the same problems (the full set takes minutes)
     seq_n = min(args.seq_sample, len(probs))
@@ -448,6 +487,8 @@ def run_batched(args):
             "config": {"workload": "batched: %d problems P in {1,2,3}, K <= 40k, n log-uniform [1e3,1e5], "
                                    "lambda log-uniform [1e-5,1e-1], tol %g, plans resident" % (len(probs), tol)},
             "converged": ok, "iterations_median": statistics.median(its), "iterations_max": max(its),
+            "cta_ms_per_problem": {"max": cta_ms[0], "top5": cta_ms[:5], "sum": sum(cta_ms),
+                                   "median": statistics.median(cta_ms)},
             "setup_s_all_plans": setup_s,
             "sequential_plain_fp64": {"solves_per_s": seq_n / seq_t, "sample": seq_n}}
     print(json.dumps(line), flush=True)
@@ -494,7 +535,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="scale", choices=["scale", "pr1", "mixed", "batched", "serving"])
+    ap.add_argument("--config", default="scale", choices=["scale", "pr1", "mixed", "batched", "serving", "paper"])
     ap.add_argument("--apply-only", action="store_true", help="time the finest-level point operator only")
     ap.add_argument("--reps", type=int, default=10)
     ap.add_argument("--launch-profile", action="store_true", help="one set-up + capped solve (ncu launch list)")
@@ -515,6 +556,8 @@ def main():
         return run_batched(args)
     if args.config == "serving":
         return run_serving(args)
+    if args.config == "paper":
+        return run_paper(args)
     pr = make_problem(args.config, args.n)
     if args.apply_only:
         return run_apply_only(args, pr)

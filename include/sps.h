@@ -94,6 +94,9 @@ typedef struct sps_options {
     int    graphs;         /* 1 (default): each PCG iteration after the first is
                               replayed from a CUDA graph captured once per set-up;
                               0: launched kernel by kernel */
+    int    precondition;   /* 1 (default): the multigrid V-cycle of Algorithm 7;
+                              0: none, i.e. plain CG, the comparison method of
+                              Section 4 (Table 2, Fig. 2) */
 } sps_options;
 
 typedef struct sps_result {

@@ -37,7 +37,7 @@ class sps_options(C.Structure):
     _fields_ = [("precision", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int), ("omega", C.c_double),
                 ("power_iters", C.c_int), ("max_iter", C.c_int), ("warm_start", C.c_int), ("tile", C.c_int),
                 ("replace_ratio", C.c_double), ("hybrid", C.c_int),
-                ("graphs", C.c_int)]
+                ("graphs", C.c_int), ("precondition", C.c_int)]
 
 
 class sps_result(C.Structure):

@@ -404,6 +404,12 @@ int solve_fp64(sps_plan* pl, double tol, sps_result* res, bool warm, cudaStream_
   int it = 0;
   int status = SPS_OK;
   double rel = 1.0;
+  // z = V(r) (Algorithm 7), or z = r for plain CG (the paper's comparison method)
+  auto precondition64 = [&](cudaStream_t s) -> int {
+    if (pl->opt.precondition) return vcycle_into<double>(pl, pl->r, pl->z, s);
+    SPS_CUDA(cudaMemcpyAsync(pl->z, pl->r, sizeof(double) * K, cudaMemcpyDeviceToDevice, s));
+    return SPS_OK;
+  };
   auto restart = [&](bool have_x) -> int {
     if (have_x) {
       SPS_TRY(apply_level<double>(pl, G, pl->x, pl->v, st));
@@ -414,7 +420,7 @@ int solve_fp64(sps_plan* pl, double tol, sps_result* res, bool warm, cudaStream_
       SPS_CUDA(cudaMemcpyAsync(pl->r, pl->rhs, sizeof(double) * K, cudaMemcpyDeviceToDevice, st));
       SPS_TRY(dot(pl, pl->r, pl->r, K, S_RR, st));
     }
-    SPS_TRY(vcycle_into<double>(pl, pl->r, pl->z, st));
+    SPS_TRY(precondition64(st));
     SPS_CUDA(cudaMemcpyAsync(pl->p, pl->z, sizeof(double) * K, cudaMemcpyDeviceToDevice, st));
     SPS_TRY(dot(pl, pl->r, pl->z, K, S_RZ_A, st));
     SPS_TRY(read_scalars(pl, st));
@@ -431,7 +437,7 @@ int solve_fp64(sps_plan* pl, double tol, sps_result* res, bool warm, cudaStream_
   };
   // z = V(r); beta = r'z / r~'z~; p = z + beta p; then the next half_apply
   auto body = [&](cudaStream_t s) -> int {
-    SPS_TRY(vcycle_into<double>(pl, pl->r, pl->z, s));
+    SPS_TRY(precondition64(s));
     SPS_TRY(dot(pl, pl->r, pl->z, K, S_RZ_B, s));
     SPS_TRY(pcg_update_p(pl, K, S_RZ_B, S_RZ_A, 0, s));
     SPS_CUDA(cudaMemcpyAsync(pl->scal + S_RZ_A, pl->scal + S_RZ_B, sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -497,6 +503,10 @@ int solve_mixed(sps_plan* pl, double tol, sps_result* res, bool warm, cudaStream
     SPS_TRY(dot(pl, pl->r, pl->r, K, S_RR, st));
   }
   auto precondition = [&](cudaStream_t s) -> int {          // z = V32(r)
+    if (!pl->opt.precondition) {
+      SPS_CUDA(cudaMemcpyAsync(pl->z, pl->r, sizeof(double) * K, cudaMemcpyDeviceToDevice, s));
+      return SPS_OK;
+    }
     SPS_TRY(vec_cast_d2f(LG.f.b, pl->r, K, s));
     SPS_TRY(vcycle_into<float>(pl, LG.f.b, a32, s));
     return vec_cast_f2d(pl->z, a32, K, s);
@@ -649,6 +659,7 @@ void sps_default_options(sps_options* opt) {
   opt->replace_ratio = 1e-2;
   opt->hybrid = 1;
   opt->graphs = 1;
+  opt->precondition = 1;
 }
 
 const char* sps_last_error(void) { return g_last_error.c_str(); }

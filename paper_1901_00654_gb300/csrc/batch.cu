@@ -56,7 +56,14 @@ struct BatchProblem {
 struct BatchOut {
   int iterations, status, fp64_applies, pad;
   double rel_res, rel_res_true;
+  double ms;               // time the CTA spent on this problem (globaltimer)
 };
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 __device__ __forceinline__ double cta_sum(double v, double* sh) {
   for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -503,9 +510,11 @@ __global__ void __launch_bounds__(BT, 1) k_batch_solve(const BatchProblem* __res
     if (q >= count) return;
     const int i = order[q];
     const BatchProblem& pb = probs[i];
+    const unsigned long long t0 = globaltimer_ns();
     if (pb.P == 1) cta_solve<1>(pb, outs + i, sh);
     else if (pb.P == 2) cta_solve<2>(pb, outs + i, sh);
     else cta_solve<3>(pb, outs + i, sh);
+    if (threadIdx.x == 0) outs[i].ms = (double)(globaltimer_ns() - t0) * 1e-6;
   }
 }
 
@@ -621,6 +630,7 @@ int solve_batch(sps_plan* const* plans, int count, double* const* coefs, int mem
       r.rel_res = out[i].rel_res;
       r.rel_res_true = out[i].rel_res_true;
       r.fp64_applies = out[i].fp64_applies;
+      r.solve_ms = out[i].ms;
     }
     if (out[i].status != SPS_OK && worst == SPS_OK) worst = out[i].status;
   }

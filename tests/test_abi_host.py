@@ -44,7 +44,7 @@ def test_struct_layouts_match_header(B):
 #include "sps.h"
 int main(void) {
   printf("%zu %zu %zu %zu %zu\n", sizeof(sps_options), offsetof(sps_options, replace_ratio),
-         offsetof(sps_options, graphs), sizeof(sps_result), offsetof(sps_result, solve_ms));
+         offsetof(sps_options, precondition), sizeof(sps_result), offsetof(sps_result, solve_ms));
   return 0;
 }
 '''
@@ -54,7 +54,7 @@ int main(void) {
         open(c, "w").write(src)
         subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
         vals = [int(v) for v in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
-    assert vals == [C.sizeof(B.sps_options), B.sps_options.replace_ratio.offset, B.sps_options.graphs.offset,
+    assert vals == [C.sizeof(B.sps_options), B.sps_options.replace_ratio.offset, B.sps_options.precondition.offset,
                     C.sizeof(B.sps_result), B.sps_result.solve_ms.offset]
 
 

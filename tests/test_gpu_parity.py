@@ -331,3 +331,21 @@ def test_graph_replay_matches_kernel_by_kernel(prec):
     (c0, i0, _, _), (c1, i1, c1b, i1b) = out
     assert abs(i0 - i1) <= 3 and abs(i1 - i1b) <= 3
     assert rel_err(c1, c0) < 1e-6 and rel_err(c1b, c1) < 1e-6
+
+
+def test_plain_cg_matches_oracle_cg():
+    """precondition = 0 is the unpreconditioned CG of Section 4 (Table 2, Fig. 2):
+    same iteration count as the oracle's CG, far more than MGCG."""
+    import workloads as W
+    pr = W.pr1()
+    H = mgcg.build_hierarchy(pr.x, pr.y, pr.lo, pr.hi, pr.intervals, 3, pr.lam, pr.levels, omega=0.3)
+    ocg = mgcg.mgcg(H, 1e-8, precondition=False, max_iter=5000)
+    with B.Plan(pr.P, pr.intervals, pr.levels, pr.lam, pr.lo, pr.hi, precondition=0) as pl:
+        pl.set_points(pr.x, pr.y)
+        coef, res = pl.solve(1e-8)
+    assert res.status == B.SPS_OK
+    assert abs(res.iterations - ocg.iterations) <= max(3, 0.05 * ocg.iterations)
+    with B.Plan(pr.P, pr.intervals, pr.levels, pr.lam, pr.lo, pr.hi) as pl:
+        pl.set_points(pr.x, pr.y)
+        _, rmg = pl.solve(1e-8)
+    assert rmg.iterations * 3 < res.iterations
