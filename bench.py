@@ -33,6 +33,7 @@ import numpy as np  # noqa: E402
 import workloads as W  # noqa: E402
 
 METRIC = "MG-PCG solves/s & operator Gpoint-applies/s at rel.res 1e-8; p50/p99 vs plain FP64"
+POINT_F64_TRAFFIC_BYTES = 101.673472e6 + 3.166464e6   # ncu dram__bytes_read.sum + dram__bytes_write.sum
 
 
 def make_problem(name: str, n: int | None):
@@ -263,8 +264,11 @@ def run_ours(args, pr):
     fma_rate = B.sps_probe_fma_rate(fp64=fp64_kernel)
     achieved = flops_launch / (avg_ms * 1e-3) / 1e12
     peak = 2.0 * fma_rate / 1e12
+    # DRAM bytes (read + write) of one FP64 apply-mode launch on this workload, from one ncu
+    # capture of the current kernel (profiles/k_point_fp64_p3_n64_1e6pts.md); None for others
+    traffic = POINT_F64_TRAFFIC_BYTES if (fp64_kernel and pr.name == "scale" and pr.n == 1_000_000) else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "k_point (apply mode), %s" % ("FP64" if fp64_kernel else "FP32/FP64 mix"),
+                "traffic": traffic, "kernel": "k_point (apply mode), %s" % ("FP64" if fp64_kernel else "FP32/FP64 mix"),
                 "flops_per_launch": flops_launch, "avg_launch_ms": avg_ms, "launches": point_launches,
                 "peak_source": "measured %s FMA probe (sps_probe_fma_rate) x 2 flops at run-time clocks"
                                % ("FP64" if fp64_kernel else "FP32")}
