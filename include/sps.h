@@ -157,9 +157,15 @@ SPS_API int sps_destroy(sps_plan* plan);
 SPS_API const char* sps_last_error(void);
 
 /* Solve `count` independent problems in ONE persistent kernel launch captured
- * in a CUDA graph: each CTA pops whole problems from a device queue (largest
- * first) and runs the mixed-precision flexible PCG of Algorithm 8 with the
- * FP32 V-cycle of Algorithm 7 entirely inside the CTA.  plans[i] must have
+ * in a CUDA graph, running the mixed-precision flexible PCG of Algorithm 8
+ * with the FP32 V-cycle of Algorithm 7 inside the kernel.  The CTAs form
+ * thread-block clusters of 2: problems costing more than the batch's total
+ * cost per CTA are taken first (largest first) from a device queue and solved
+ * each by a whole cluster; then every CTA takes the remaining problems alone.
+ * The environment variable SPS_BATCH_CLUSTER (1, 2, 4 or 8), read at each
+ * call, sets another cluster size; 1 gives one CTA per problem throughout.
+ * Results agree with sps_solve to the solve's tolerance (the summation order
+ * differs).  plans[i] must have
  * P <= 3 and points set; coefs[i] receives K_G(i) doubles in `mem`; tol is
  * shared; results may be NULL (else `count` entries).  Each plan's buffers are
  * used, so a plan must not be in another call at the same time.  Returns the

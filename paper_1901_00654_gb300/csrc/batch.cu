@@ -1,18 +1,22 @@
 // Batched solves: many independent smoothing problems in one persistent
 // kernel launch, captured in a CUDA graph.
 //
-// Each CTA takes whole problems from a device-side queue (largest first) and
-// runs the complete mixed-precision flexible PCG of one problem -- FP32
-// V-cycle (Algorithm 7 with Algorithm 6) and FP32 point operator, FP64 outer
-// vectors, dot products, residual replacement and coarse solve -- with
-// __syncthreads() between the phases.  Small problems (K <= 40k, n <= 1e5)
+// A team of CTAs takes whole problems from a device-side queue (largest
+// first) and runs the complete mixed-precision flexible PCG of one problem --
+// FP32 V-cycle (Algorithm 7 with Algorithm 6) and FP32 point operator, FP64
+// outer vectors, dot products, residual replacement and coarse solve -- with
+// a barrier between the phases.  A team is a thread-block cluster for the
+// largest problems (loops split across its CTAs, cluster barriers, dot
+// products through distributed shared memory) and a single CTA for the rest.  Small problems (K <= 40k, n <= 1e5)
 // are launch-latency bound when each step is its own kernel; here a
 // problem's whole solve costs one queue pop.  Problems with P <= 3 only (one
 // lane per run).
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -65,7 +69,26 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
   return t;
 }
 
-__device__ __forceinline__ double cta_sum(double v, double* sh) {
+namespace cg = cooperative_groups;
+
+// The CTAs that solve one problem together: one CTA, or a thread-block
+// cluster whose CTAs split every loop and meet at cluster barriers.
+struct Team {
+  int rank, size, phase;
+  __device__ long long start() const { return (long long)rank * BT + threadIdx.x; }
+  __device__ long long stride() const { return (long long)size * BT; }
+};
+
+__device__ __forceinline__ void team_sync(const Team& tm) {
+  if (tm.size == 1) __syncthreads();
+  else cg::this_cluster().sync();
+}
+
+// Sum over every thread of the team, the same value in every thread (fixed
+// order: every CTA of a cluster gets bitwise the same total, so all of them
+// take the same branches).
+__device__ __forceinline__ double team_sum(double v, double* sh, Team& tm) {
+  __shared__ double slot[2];
   for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   __syncthreads();
@@ -73,7 +96,14 @@ __device__ __forceinline__ double cta_sum(double v, double* sh) {
   __syncthreads();
   double t = 0.0;
   for (int w = 0; w < BT / 32; ++w) t += sh[w];
-  return t;   // same value in every thread
+  if (tm.size == 1) return t;
+  cg::cluster_group cl = cg::this_cluster();
+  if (threadIdx.x == 0) slot[tm.phase] = t;
+  cl.sync();
+  double tot = 0.0;
+  for (int r = 0; r < tm.size; ++r) tot += *cl.map_shared_rank(&slot[tm.phase], r);
+  tm.phase ^= 1;   // the other slot next time: readers of this one pass the next barrier first
+  return tot;
 }
 
 template <typename T>
@@ -90,10 +120,10 @@ __device__ __forceinline__ void cubic(T t, T* b) {
 // sums of the cell's (q+1)^P coefficients in registers, one global atomic per
 // coefficient per run.
 template <int P, typename T>
-__device__ void cta_point(const BatchProblem& pb, const BatchLevel& L, const T* v, T* u) {
+__device__ void cta_point(const BatchProblem& pb, const BatchLevel& L, const T* v, T* u, const Team& tm) {
   constexpr int NR = 1 << (2 * P);
   const LevelGeom& g = L.geom;
-  for (int r = threadIdx.x; r < L.nruns; r += BT) {
+  for (long long r = tm.start(); r < L.nruns; r += tm.stride()) {
     const int i0 = L.run_begin[r], i1 = L.run_begin[r + 1];
     const unsigned long long pc = L.run_cell[r];
     long long base = 0;
@@ -179,7 +209,8 @@ __device__ void cta_point(const BatchProblem& pb, const BatchLevel& L, const T* 
 // u = scale * Lambda_g v by the three-term Kronecker recursion (one sweep per
 // dimension, temporaries t[0..5]).
 template <typename T>
-__device__ void cta_penalty(const LevelGeom& g, const T* band, const T* v, T* out, T scale, T* const* t) {
+__device__ void cta_penalty(const LevelGeom& g, const T* band, const T* v, T* out, T scale, T* const* t,
+                            const Team& tm) {
   const int P = g.P;
   const long long K = g.K;
   const T* in0 = v;
@@ -197,7 +228,7 @@ __device__ void cta_penalty(const LevelGeom& g, const T* band, const T* v, T* ou
     T* o0 = t[3 * ping];
     T* o1 = t[3 * ping + 1];
     T* o2 = t[3 * ping + 2];
-    for (long long k = threadIdx.x; k < K; k += BT) {
+    for (long long k = tm.start(); k < K; k += tm.stride()) {
       const int j = (int)((k / strd) % Jp);
       T a0 = T(0), a1 = T(0), a2 = T(0);
       for (int o = -Q; o <= Q; ++o) {
@@ -225,7 +256,7 @@ __device__ void cta_penalty(const LevelGeom& g, const T* band, const T* v, T* ou
         o2[k] = a2;
       }
     }
-    __syncthreads();
+    team_sync(tm);
     in0 = o0;
     in1 = o1;
     in2 = o2;
@@ -235,11 +266,12 @@ __device__ void cta_penalty(const LevelGeom& g, const T* band, const T* v, T* ou
 }
 
 template <int P, typename T>
-__device__ void cta_apply(const BatchProblem& pb, int lev, const T* v, T* u, T* const* t, const T* band) {
+__device__ void cta_apply(const BatchProblem& pb, int lev, const T* v, T* u, T* const* t, const T* band,
+                          const Team& tm) {
   const BatchLevel& L = pb.lev[lev - 1];
   if (sizeof(T) == 4 && L.st_f) {
     const LevelGeom& g = L.geom;
-    for (long long k = threadIdx.x; k < g.K; k += BT) {
+    for (long long k = tm.start(); k < g.K; k += tm.stride()) {
       int j[P];
       for (int p = 0; p < P; ++p) j[p] = (int)((k / g.stride[p]) % g.J[p]);
       T acc = T(0);
@@ -257,16 +289,17 @@ __device__ void cta_apply(const BatchProblem& pb, int lev, const T* v, T* u, T* 
       }
       u[k] = acc;
     }
-    __syncthreads();
+    team_sync(tm);
     return;
   }
-  cta_penalty<T>(L.geom, band, v, u, T(pb.lam), t);
-  cta_point<P, T>(pb, L, v, u);
-  __syncthreads();
+  cta_penalty<T>(L.geom, band, v, u, T(pb.lam), t, tm);
+  cta_point<P, T>(pb, L, v, u, tm);
+  team_sync(tm);
 }
 
 // c = I'(f - fb) (fb may be null); P sweeps through t6/t7.
-__device__ void cta_restrict(const BatchProblem& pb, int g, const float* f, const float* fb, float* c) {
+__device__ void cta_restrict(const BatchProblem& pb, int g, const float* f, const float* fb, float* c,
+                             const Team& tm) {
   const LevelGeom& Gf = pb.lev[g - 1].geom;
   const LevelGeom& Gc = pb.lev[g - 2].geom;
   const float* in = f;
@@ -278,7 +311,7 @@ __device__ void cta_restrict(const BatchProblem& pb, int g, const float* f, cons
     const int Jin = Gf.J[p], Jout = Gc.J[p];
     const long long Kout = outer * Jout * inner;
     float* out = p == pb.P - 1 ? c : pb.ftmp[6 + (p & 1)];
-    for (long long k = threadIdx.x; k < Kout; k += BT) {
+    for (long long k = tm.start(); k < Kout; k += tm.stride()) {
       const long long o = k / ((long long)Jout * inner);
       const long long rem = k - o * Jout * inner;
       const int j = (int)(rem / inner);
@@ -294,14 +327,14 @@ __device__ void cta_restrict(const BatchProblem& pb, int g, const float* f, cons
       }
       out[k] = s;
     }
-    __syncthreads();
+    team_sync(tm);
     in = out;
     inb = nullptr;
   }
 }
 
 // f -= I c.
-__device__ void cta_prolong_sub(const BatchProblem& pb, int g, const float* c, float* f) {
+__device__ void cta_prolong_sub(const BatchProblem& pb, int g, const float* c, float* f, const Team& tm) {
   const LevelGeom& Gf = pb.lev[g - 1].geom;
   const LevelGeom& Gc = pb.lev[g - 2].geom;
   const float* in = c;
@@ -313,7 +346,7 @@ __device__ void cta_prolong_sub(const BatchProblem& pb, int g, const float* c, f
     const long long Kout = outer * Jout * inner;
     const bool last = p == pb.P - 1;
     float* out = last ? f : pb.ftmp[6 + (p & 1)];
-    for (long long k = threadIdx.x; k < Kout; k += BT) {
+    for (long long k = tm.start(); k < Kout; k += tm.stride()) {
       const long long o = k / ((long long)Jout * inner);
       const long long rem = k - o * Jout * inner;
       const int i = (int)(rem / inner);
@@ -329,14 +362,14 @@ __device__ void cta_prolong_sub(const BatchProblem& pb, int g, const float* c, f
       }
       if (last) out[k] -= s; else out[k] = s;
     }
-    __syncthreads();
+    team_sync(tm);
     in = out;
   }
 }
 
 // alpha_G = V(b_G), FP32 (Algorithm 7 from zero).
 template <int P>
-__device__ void cta_vcycle(const BatchProblem& pb, const float* bG, float* xG) {
+__device__ void cta_vcycle(const BatchProblem& pb, const float* bG, float* xG, const Team& tm) {
   const int G = pb.G;
   float* const* t = pb.ftmp;
   auto B = [&](int g) -> float* { return g == G ? const_cast<float*>(bG) : pb.lev[g - 1].b; };
@@ -346,47 +379,47 @@ __device__ void cta_vcycle(const BatchProblem& pb, const float* bG, float* xG) {
     const long long K = L.geom.K;
     float* x = X(g);
     const float* b = B(g);
-    for (long long k = threadIdx.x; k < K; k += BT) x[k] = pb.nu1 >= 1 ? L.omega * L.dinv[k] * b[k] : 0.0f;
-    __syncthreads();
+    for (long long k = tm.start(); k < K; k += tm.stride()) x[k] = pb.nu1 >= 1 ? L.omega * L.dinv[k] * b[k] : 0.0f;
+    team_sync(tm);
     for (int s = 1; s < pb.nu1; ++s) {
-      cta_apply<P, float>(pb, g, x, L.u, t, L.band);
-      for (long long k = threadIdx.x; k < K; k += BT) x[k] = fmaf(L.omega * L.dinv[k], b[k] - L.u[k], x[k]);
-      __syncthreads();
+      cta_apply<P, float>(pb, g, x, L.u, t, L.band, tm);
+      for (long long k = tm.start(); k < K; k += tm.stride()) x[k] = fmaf(L.omega * L.dinv[k], b[k] - L.u[k], x[k]);
+      team_sync(tm);
     }
-    if (pb.nu1 >= 1) cta_apply<P, float>(pb, g, x, L.u, t, L.band);
+    if (pb.nu1 >= 1) cta_apply<P, float>(pb, g, x, L.u, t, L.band, tm);
     else {
-      for (long long k = threadIdx.x; k < K; k += BT) L.u[k] = 0.0f;
-      __syncthreads();
+      for (long long k = tm.start(); k < K; k += tm.stride()) L.u[k] = 0.0f;
+      team_sync(tm);
     }
-    cta_restrict(pb, g, L.u, b, B(g - 1));
+    cta_restrict(pb, g, L.u, b, B(g - 1), tm);
   }
   {
     const long long K1 = pb.lev[0].geom.K;
     const float* b1 = B(1);
     float* x1 = X(1);
-    for (long long row = threadIdx.x; row < K1; row += BT) {
+    for (long long row = tm.start(); row < K1; row += tm.stride()) {
       double s = 0.0;
       for (long long c = 0; c < K1; ++c) s = fma(pb.coarse_inv[row * K1 + c], (double)b1[c], s);
       x1[row] = (float)s;
     }
-    __syncthreads();
+    team_sync(tm);
   }
   for (int g = 2; g <= G; ++g) {
     const BatchLevel& L = pb.lev[g - 1];
     const long long K = L.geom.K;
     float* x = X(g);
     const float* b = B(g);
-    cta_prolong_sub(pb, g, X(g - 1), x);
+    cta_prolong_sub(pb, g, X(g - 1), x, tm);
     for (int s = 0; s < pb.nu2; ++s) {
-      cta_apply<P, float>(pb, g, x, L.u, t, L.band);
-      for (long long k = threadIdx.x; k < K; k += BT) x[k] = fmaf(L.omega * L.dinv[k], b[k] - L.u[k], x[k]);
-      __syncthreads();
+      cta_apply<P, float>(pb, g, x, L.u, t, L.band, tm);
+      for (long long k = tm.start(); k < K; k += tm.stride()) x[k] = fmaf(L.omega * L.dinv[k], b[k] - L.u[k], x[k]);
+      team_sync(tm);
     }
   }
 }
 
 template <int P>
-__device__ void cta_solve(const BatchProblem& pb, BatchOut* out, double* sh) {
+__device__ void cta_solve(const BatchProblem& pb, BatchOut* out, double* sh, Team& tm) {
   double* const* dt = pb.dtmp;
   const int G = pb.G;
   const BatchLevel& LG = pb.lev[G - 1];
@@ -402,65 +435,65 @@ __device__ void cta_solve(const BatchProblem& pb, BatchOut* out, double* sh) {
   float* a32 = LG.alpha;
   float* v32 = pb.ftmp[7];
   auto fp64_residual = [&]() -> double {   // r = rhs - A x in FP64 (Alg. 8 residual, recomputed)
-    cta_penalty<double>(LG.geom, LG.band_d, x, v, pb.lam, dt);
-    cta_point<P, double>(pb, LG, x, v);
-    __syncthreads();
+    cta_penalty<double>(LG.geom, LG.band_d, x, v, pb.lam, dt, tm);
+    cta_point<P, double>(pb, LG, x, v, tm);
+    team_sync(tm);
     double s = 0.0;
-    for (long long k = threadIdx.x; k < K; k += BT) {
+    for (long long k = tm.start(); k < K; k += tm.stride()) {
       const double rk = pb.rhs[k] - v[k];
       r[k] = rk;
       s = fma(rk, rk, s);
     }
-    return cta_sum(s, sh);
+    return team_sum(s, sh, tm);
   };
   auto precondition = [&]() {
-    for (long long k = threadIdx.x; k < K; k += BT) b32[k] = (float)r[k];
-    __syncthreads();
-    cta_vcycle<P>(pb, b32, a32);
-    for (long long k = threadIdx.x; k < K; k += BT) z[k] = (double)a32[k];
-    __syncthreads();
+    for (long long k = tm.start(); k < K; k += tm.stride()) b32[k] = (float)r[k];
+    team_sync(tm);
+    cta_vcycle<P>(pb, b32, a32, tm);
+    for (long long k = tm.start(); k < K; k += tm.stride()) z[k] = (double)a32[k];
+    team_sync(tm);
   };
   double s = 0.0;
-  for (long long k = threadIdx.x; k < K; k += BT) {
+  for (long long k = tm.start(); k < K; k += tm.stride()) {
     x[k] = 0.0;
     r[k] = pb.rhs[k];
     s = fma(r[k], r[k], s);
   }
-  double rr = cta_sum(s, sh);
+  double rr = team_sum(s, sh, tm);
   double rlast = sqrt(rr);
   double rel = rlast / nb;
   int it = 0, status = SPS_OK, f64 = 0;
   precondition();
   s = 0.0;
-  for (long long k = threadIdx.x; k < K; k += BT) {
+  for (long long k = tm.start(); k < K; k += tm.stride()) {
     p[k] = z[k];
     s = fma(r[k], z[k], s);
   }
-  double rz = cta_sum(s, sh);
+  double rz = team_sum(s, sh, tm);
   while (rel > pb.tol && it < pb.max_iter) {
-    for (long long k = threadIdx.x; k < K; k += BT) pb.p32[k] = (float)p[k];
-    __syncthreads();
-    cta_apply<P, float>(pb, G, pb.p32, v32, pb.ftmp, LG.band);
+    for (long long k = tm.start(); k < K; k += tm.stride()) pb.p32[k] = (float)p[k];
+    team_sync(tm);
+    cta_apply<P, float>(pb, G, pb.p32, v32, pb.ftmp, LG.band, tm);
     s = 0.0;
-    for (long long k = threadIdx.x; k < K; k += BT) {
+    for (long long k = tm.start(); k < K; k += tm.stride()) {
       v[k] = (double)v32[k];
       s = fma(p[k], v[k], s);
     }
-    const double pv = cta_sum(s, sh);
+    const double pv = team_sum(s, sh, tm);
     const double w = rz / pv;
     if (!(pv > 0.0) || !isfinite(w)) {
       status = SPS_EBREAKDOWN;
       break;
     }
     s = 0.0;
-    for (long long k = threadIdx.x; k < K; k += BT) {
+    for (long long k = tm.start(); k < K; k += tm.stride()) {
       rp[k] = r[k];
       x[k] = fma(w, p[k], x[k]);
       const double rk = fma(-w, v[k], r[k]);
       r[k] = rk;
       s = fma(rk, rk, s);
     }
-    rr = cta_sum(s, sh);
+    rr = team_sum(s, sh, tm);
     ++it;
     double rn = sqrt(rr);
     rel = rn / nb;
@@ -474,47 +507,70 @@ __device__ void cta_solve(const BatchProblem& pb, BatchOut* out, double* sh) {
     }
     precondition();
     double s1 = 0.0, s2 = 0.0;
-    for (long long k = threadIdx.x; k < K; k += BT) {
+    for (long long k = tm.start(); k < K; k += tm.stride()) {
       s1 = fma(z[k], r[k], s1);
       s2 = fma(z[k], rp[k], s2);
     }
-    const double zr = cta_sum(s1, sh);
-    const double zrp = cta_sum(s2, sh);
+    const double zr = team_sum(s1, sh, tm);
+    const double zrp = team_sum(s2, sh, tm);
     const double beta = (zr - zrp) / rz;
-    for (long long k = threadIdx.x; k < K; k += BT) p[k] = fma(beta, p[k], z[k]);
-    __syncthreads();
+    for (long long k = tm.start(); k < K; k += tm.stride()) p[k] = fma(beta, p[k], z[k]);
+    team_sync(tm);
     rz = zr;
   }
   const double rt = sqrt(fp64_residual()) / nb;
   ++f64;
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0 && tm.rank == 0) {
     out->iterations = it;
     out->rel_res = rel;
     out->rel_res_true = rt;
     out->fp64_applies = f64;
     out->status = status != SPS_OK ? status : (rt <= pb.tol ? SPS_OK : SPS_ENOCONV);
   }
-  __syncthreads();
+  team_sync(tm);
 }
 
+// Persistent batched solver.  Phase 1 (C > 1): each cluster takes the next
+// of the nbig largest problems from queue[0] and solves it with all C CTAs.
+// Phase 2: every CTA takes the next remaining problem from queue[1] and
+// solves it alone.  Problems arrive in decreasing cost order.
+template <int C>
 __global__ void __launch_bounds__(BT, 1) k_batch_solve(const BatchProblem* __restrict__ probs,
-                                                       const int* __restrict__ order, int count, int* queue,
-                                                       BatchOut* __restrict__ outs) {
+                                                       const int* __restrict__ order, int count, int nbig,
+                                                       int* queue, BatchOut* __restrict__ outs) {
   __shared__ double sh[BT / 32];
   __shared__ int cur;
+  Team tm;
+  tm.size = C;
+  tm.rank = C > 1 ? (int)cg::this_cluster().block_rank() : 0;
+  tm.phase = 0;
   for (;;) {
-    if (threadIdx.x == 0) cur = atomicAdd(queue, 1);
-    __syncthreads();
-    const int q = cur;
-    __syncthreads();
-    if (q >= count) return;
+    int q;
+    if (tm.size > 1) {
+      cg::cluster_group cl = cg::this_cluster();
+      if (threadIdx.x == 0 && tm.rank == 0) cur = atomicAdd(&queue[0], 1);
+      cl.sync();
+      q = *cl.map_shared_rank(&cur, 0);
+      cl.sync();   // every CTA has read rank 0's slot before it is written again or the CTAs part
+      if (q >= nbig) {
+        tm.size = 1;   // phase 2: this CTA alone
+        tm.rank = 0;
+        continue;
+      }
+    } else {
+      if (threadIdx.x == 0) cur = atomicAdd(&queue[1], 1);
+      __syncthreads();
+      q = nbig + cur;
+      __syncthreads();
+      if (q >= count) return;
+    }
     const int i = order[q];
     const BatchProblem& pb = probs[i];
     const unsigned long long t0 = globaltimer_ns();
-    if (pb.P == 1) cta_solve<1>(pb, outs + i, sh);
-    else if (pb.P == 2) cta_solve<2>(pb, outs + i, sh);
-    else cta_solve<3>(pb, outs + i, sh);
-    if (threadIdx.x == 0) outs[i].ms = (double)(globaltimer_ns() - t0) * 1e-6;
+    if (pb.P == 1) cta_solve<1>(pb, outs + i, sh, tm);
+    else if (pb.P == 2) cta_solve<2>(pb, outs + i, sh, tm);
+    else cta_solve<3>(pb, outs + i, sh, tm);
+    if (threadIdx.x == 0 && tm.rank == 0) outs[i].ms = (double)(globaltimer_ns() - t0) * 1e-6;
   }
 }
 
@@ -594,16 +650,85 @@ int solve_batch(sps_plan* const* plans, int count, double* const* coefs, int mem
   int sms = 0, devid = 0;
   SPS_CUDA(cudaGetDevice(&devid));
   SPS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, devid));
-  const int grid = std::min(count, sms);
+  // Problems whose cost exceeds a balanced share of the whole batch per CTA
+  // would bound the batch's time if solved by one CTA: thread-block clusters
+  // of C CTAs (C = 2 unless SPS_BATCH_CLUSTER says 1, 4 or 8) solve those
+  // together first, then every CTA takes the rest alone.  Each phase of a
+  // solve is short, so cluster barriers soon cost more than the extra CTAs
+  // gain: on the 512-problem batch C = 2 gave the shortest batch time.
+  int C = 2;
+  if (const char* e = getenv("SPS_BATCH_CLUSTER")) {
+    const int c = atoi(e);
+    if (c == 1 || c == 2 || c == 4 || c == 8) C = c;
+  }
+  int grid = std::min(count, sms);
+  if (C > 1) {
+    cudaLaunchConfig_t oc = {};
+    oc.gridDim = dim3(((sms + C - 1) / C) * C);
+    oc.blockDim = dim3(BT);
+    cudaLaunchAttribute oa;
+    oa.id = cudaLaunchAttributeClusterDimension;
+    oa.val.clusterDim.x = C;
+    oa.val.clusterDim.y = 1;
+    oa.val.clusterDim.z = 1;
+    oc.attrs = &oa;
+    oc.numAttrs = 1;
+    int clusters = 0;
+    cudaError_t oe = C == 2 ? cudaOccupancyMaxActiveClusters(&clusters, k_batch_solve<2>, &oc)
+                     : C == 4 ? cudaOccupancyMaxActiveClusters(&clusters, k_batch_solve<4>, &oc)
+                              : cudaOccupancyMaxActiveClusters(&clusters, k_batch_solve<8>, &oc);
+    if (oe != cudaSuccess || clusters < 1) {
+      cudaGetLastError();
+      C = 1;
+    } else {
+      grid = clusters * C;
+    }
+  }
+  int nbig = 0;
+  if (C > 1) {
+    double total = 0.0;
+    for (int i = 0; i < count; ++i) total += cost[i];
+    const double share = total / grid;
+    while (nbig < count && cost[order[nbig]] > share) ++nbig;
+  }
   // capture: reset the queue, then the persistent kernel
   cudaGraph_t graph;
   cudaGraphExec_t exec;
   cudaStream_t cs;
   SPS_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   SPS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-  cudaMemsetAsync(dev + off_q, 0, sizeof(int), cs);
-  k_batch_solve<<<grid, BT, 0, cs>>>((const BatchProblem*)dev, (const int*)(dev + off_o), count, (int*)(dev + off_q),
-                                     (BatchOut*)(dev + off_r));
+  cudaMemsetAsync(dev + off_q, 0, 2 * sizeof(int), cs);
+  {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(BT);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = cs;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const BatchProblem* a0 = (const BatchProblem*)dev;
+    const int* a1 = (const int*)(dev + off_o);
+    int* a3 = (int*)(dev + off_q);
+    BatchOut* a4 = (BatchOut*)(dev + off_r);
+    cudaError_t le;
+    switch (C) {
+      case 1: le = cudaLaunchKernelEx(&cfg, k_batch_solve<1>, a0, a1, count, nbig, a3, a4); break;
+      case 2: le = cudaLaunchKernelEx(&cfg, k_batch_solve<2>, a0, a1, count, nbig, a3, a4); break;
+      case 4: le = cudaLaunchKernelEx(&cfg, k_batch_solve<4>, a0, a1, count, nbig, a3, a4); break;
+      default: le = cudaLaunchKernelEx(&cfg, k_batch_solve<8>, a0, a1, count, nbig, a3, a4); break;
+    }
+    if (le != cudaSuccess) {
+      cudaGraph_t dummy;
+      cudaStreamEndCapture(cs, &dummy);
+      cudaStreamDestroy(cs);
+      return cuda_fail(le, "batched launch");
+    }
+  }
   SPS_CUDA(cudaStreamEndCapture(cs, &graph));
   SPS_CUDA(cudaGraphInstantiate(&exec, graph, 0));
   count_launches(1);
