@@ -97,6 +97,18 @@ typedef struct sps_options {
     int    precondition;   /* 1 (default): the multigrid V-cycle of Algorithm 7;
                               0: none, i.e. plain CG, the comparison method of
                               Section 4 (Table 2, Fig. 2) */
+    int    autotune;       /* 1: on the plan's first sps_set_points, time the
+                              point operator of every matrix-free level with
+                              tile sides ts/2, ts, 2ts (and, in the mixed mode
+                              for P = 3, 4, both lane layouts per run) and keep
+                              the fastest; the operator is the same matrix.
+                              0 (default): fixed tile side per P */
+    int    lanes_r;        /* FP32 apply of the point operator for P = 3, 4:
+                              dimensions of a run's (q+1)^P coefficients held in
+                              one lane's registers, 2 (4^(P-2) lanes per run,
+                              16 sums each) or 3 (4^(P-3) lanes, 64 sums);
+                              0 (default): 2 for P = 3, 3 for P = 4.  Ignored
+                              for other P; the autotuner may change it */
 } sps_options;
 
 typedef struct sps_result {
@@ -173,6 +185,13 @@ SPS_API const char* sps_last_error(void);
  * `stream`. */
 SPS_API int sps_solve_batch(sps_plan* const* plans, int count, double* const* coefs, int mem, double tol,
                             sps_result* results, void* stream);
+
+/* Launch shape of level `level`'s point operator (after sps_set_points):
+ * tile side in cells and, for the FP32 apply, the dimensions held in one
+ * lane's registers (2 or 3; 0 = the default for P).  Not a step of the
+ * paper's method: it reports what sps_options.autotune chose.
+ * Errors: SPS_EINVAL (NULL or level out of range). */
+SPS_API int sps_get_tuning(const sps_plan* plan, int level, int* tile, int* lanes_r);
 
 /* ---------------- component entry points (each one step of the solve) ----------------
  * All vectors are doubles in `mem`; `prec` selects the FP64 kernels

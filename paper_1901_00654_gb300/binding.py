@@ -30,14 +30,15 @@ EXPORTED = ["sps_default_options", "sps_plan_create", "sps_set_points", "sps_sol
             "sps_prolong", "sps_restrict", "sps_coarse_solve", "sps_vcycle", "sps_get_sort", "sps_get_omega",
             "sps_set_omega", "sps_probe_fma_rate", "sps_point_apply", "sps_launch_count",
             "sps_profile_begin", "sps_profile_end", "sps_solve_batch", "sps_set_lambda",
-            "sps_penalty_apply_noalloc"]
+            "sps_penalty_apply_noalloc", "sps_get_tuning"]
 
 
 class sps_options(C.Structure):
     _fields_ = [("precision", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int), ("omega", C.c_double),
                 ("power_iters", C.c_int), ("max_iter", C.c_int), ("warm_start", C.c_int), ("tile", C.c_int),
                 ("replace_ratio", C.c_double), ("hybrid", C.c_int),
-                ("graphs", C.c_int), ("precondition", C.c_int)]
+                ("graphs", C.c_int), ("precondition", C.c_int), ("autotune", C.c_int),
+                ("lanes_r", C.c_int)]
 
 
 class sps_result(C.Structure):
@@ -76,6 +77,7 @@ def load(path: str | None = None) -> C.CDLL:
         "sps_vcycle": (I, [P, I, P, P, I, P]),
         "sps_get_sort": (I, [P, P, P, I, P]),
         "sps_get_omega": (I, [P, P]),
+        "sps_get_tuning": (I, [P, I, P, P]),
         "sps_set_omega": (I, [P, P]),
         "sps_probe_fma_rate": (I, [I, C.POINTER(D), P]),
         "sps_point_apply": (I, [P, I, I, P, P, I, P]),
@@ -303,6 +305,13 @@ def sps_get_omega(plan, levels) -> np.ndarray:
     out = np.zeros(levels)
     _check(lib().sps_get_omega(plan, C.c_void_p(out.ctypes.data)), "sps_get_omega")
     return out
+
+
+def sps_get_tuning(plan, level) -> tuple:
+    """(tile side, lanes layout) of a level's point operator."""
+    ts, lr = C.c_int(0), C.c_int(0)
+    _check(lib().sps_get_tuning(plan, level, C.byref(ts), C.byref(lr)), "sps_get_tuning")
+    return ts.value, lr.value
 
 
 def sps_set_omega(plan, omega) -> None:

@@ -120,11 +120,6 @@ int alloc(T** p, long long count) {
   return SPS_OK;
 }
 
-#define SPS_TRY(x)          \
-  do {                      \
-    int _r = (x);           \
-    if (_r != SPS_OK) return _r; \
-  } while (0)
 
 __global__ void k_hash_fill(double* x, long long n, unsigned long long seed) {
   // SplitMix64 (Steele, Lea, Flood 2014) in counter mode, mapped to [-1, 1).
@@ -643,6 +638,22 @@ int run_f32(long long nin, long long nout, const double* in, double* out, F&& fn
 
 using namespace sps;
 
+namespace sps {
+void level_tile(LevelGeom& G, int ts) {
+  G.ts = ts;
+  for (int p = 0; p < G.P; ++p) {
+    G.E[p] = std::min(ts, G.N[p]) + Q;
+    G.invE[p] = 1.0f / (float)G.E[p];
+  }
+  int es = 1;
+  for (int p = G.P - 1; p >= 0; --p) {
+    G.Es[p] = es;
+    es *= G.E[p];
+  }
+  G.patch = es;
+}
+}  // namespace sps
+
 extern "C" {
 
 void sps_default_options(sps_options* opt) {
@@ -660,6 +671,8 @@ void sps_default_options(sps_options* opt) {
   opt->hybrid = 1;
   opt->graphs = 1;
   opt->precondition = 1;
+  opt->autotune = 0;
+  opt->lanes_r = 0;
 }
 
 const char* sps_last_error(void) { return g_last_error.c_str(); }
@@ -691,7 +704,8 @@ int sps_plan_create(sps_plan** out, int P, int q, const int* intervals, const do
   sps_default_options(&o);
   if (opt) o = *opt;
   if (o.nu1 < 0 || o.nu2 < 0 || o.max_iter < 1 || (o.precision != SPS_PREC_FP64 && o.precision != SPS_PREC_MIXED) ||
-      o.tile < 0 || (o.tile & (o.tile - 1)) != 0) {
+      o.tile < 0 || (o.tile & (o.tile - 1)) != 0 || (o.autotune != 0 && o.autotune != 1) ||
+      (o.lanes_r != 0 && o.lanes_r != 2 && o.lanes_r != 3)) {
     set_error("invalid options");
     return SPS_EINVAL;
   }
@@ -752,15 +766,9 @@ int sps_plan_create(sps_plan** out, int P, int q, const int* intervals, const do
       G.K *= G.J[p];
       G.lo[p] = pl->lo[p];
       G.inv_h[p] = (double)G.N[p] / (pl->hi[p] - pl->lo[p]);
-      G.E[p] = std::min(G.ts, G.N[p]) + Q;
-      G.invE[p] = 1.0f / (float)G.E[p];
     }
-    int es = 1;
-    for (int p = P - 1; p >= 0; --p) {
-      G.Es[p] = es;
-      es *= G.E[p];
-    }
-    G.patch = es;
+    level_tile(G, G.ts);
+    pl->lev[g - 1].lanes_r = (P == 3 || P == 4) ? o.lanes_r : 0;
     if (g == 1 && G.K > COARSE_MAX) {
       set_error("coarsest level too large for the dense coarse solve (K_1 > 4096): add levels");
       rc = SPS_EINVAL;
@@ -975,6 +983,10 @@ int sps_set_points(sps_plan* pl, int64_t n, const void* x, const void* y, int dt
       }
       SPS_TRY(basis_precompute(pl, g, st));
     }
+  }
+  if (pl->opt.autotune && !pl->tuned) {
+    SPS_TRY(autotune(pl, st));
+    pl->tuned = true;
   }
   for (int g = 2; g <= G; ++g) {
     if (pl->opt.omega > 0.0) pl->lev[g - 1].omega = pl->opt.omega;
@@ -1236,6 +1248,16 @@ int sps_get_sort(sps_plan* pl, int64_t* perm, uint64_t* key, int mem, void* stre
                              mem == SPS_MEM_HOST ? cudaMemcpyHostToHost : cudaMemcpyHostToDevice, st));
   }
   SPS_CUDA(cudaStreamSynchronize(st));
+  return SPS_OK;
+}
+
+int sps_get_tuning(const sps_plan* pl, int level, int* tile, int* lanes_r) {
+  if (!pl || level < 1 || level > pl->G) {
+    set_error("invalid plan or level");
+    return SPS_EINVAL;
+  }
+  if (tile) *tile = pl->lev[level - 1].geom.ts;
+  if (lanes_r) *lanes_r = pl->lev[level - 1].lanes_r;
   return SPS_OK;
 }
 

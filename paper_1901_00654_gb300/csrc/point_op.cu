@@ -77,6 +77,24 @@ k_point(const WorkItem* __restrict__ items, const int* __restrict__ run_begin,
   const WorkItem it = items[blockIdx.x];
   const int pbeg = run_begin[it.run_lo];
   const int npts = run_begin[it.run_hi] - pbeg;
+  // The item's run table (in processing order) is staged in shared memory with
+  // the coordinates, so the run loop reads no global memory before its points.
+  // Items hold at most MAXR runs by construction (the item builder's cap).
+  constexpr int MAXR = 128;
+  constexpr int CB = 32 / P;                        // bits per dimension of a packed cell offset
+  constexpr unsigned CMASK = CB >= 32 ? 0xffffffffu : (1u << CB) - 1u;
+  __shared__ unsigned int s_span[MAXR];             // first | end << 16, relative to pbeg
+  __shared__ unsigned int s_cell[MAXR];             // cell - tile origin, CB bits per dimension
+  const int nr = min(it.run_hi - it.run_lo, MAXR);
+  for (int e = threadIdx.x; e < nr; e += blockDim.x) {
+    const int r = run_order[it.run_lo + e];
+    const unsigned long long pc = run_cell[r];
+    unsigned cl = 0;
+#pragma unroll
+    for (int p = 0; p < P; ++p) cl |= (unsigned)((int)((pc >> (12 * p)) & 0xFFFull) - it.c0[p]) << (CB * p);
+    s_span[e] = (unsigned)(run_begin[r] - pbeg) | ((unsigned)(run_begin[r + 1] - pbeg) << 16);
+    s_cell[e] = cl;
+  }
   if (!PRE) {
 #pragma unroll
     for (int p = 0; p < P; ++p)
@@ -118,25 +136,43 @@ k_point(const WorkItem* __restrict__ items, const int* __restrict__ run_begin,
       l >>= 2;
     }
   }
-  T inv[P];
+  T inv[P], loinv[P];
 #pragma unroll
-  for (int p = 0; p < P; ++p) inv[p] = T(geom.inv_h[p]);
+  for (int p = 0; p < P; ++p) {
+    inv[p] = T(geom.inv_h[p]);
+    loinv[p] = T(geom.lo[p] * geom.inv_h[p]);
+  }
+  // A lane needs only piece mfix[p] of the cubic in each fixed dimension: its
+  // power-basis coefficients c0 + c1 t + c2 t^2 + c3 t^3, from the four pieces
+  // (1-t)^3/6, (3t^3-6t^2+4)/6, (-3t^3+3t^2+3t+1)/6 and t^3/6.  Used by the
+  // register-light layouts (RR > 0); elsewhere the 4F extra registers would
+  // cost occupancy, and the lane evaluates all four pieces and selects.
+  constexpr bool ONEPIECE = RR > 0 && F > 0;
+  constexpr int NF = ONEPIECE ? F : 1;
+  T pc0[NF], pc1[NF], pc2[NF], pc3[NF];
+#pragma unroll
+  for (int p = 0; p < (ONEPIECE ? F : 0); ++p) {
+    const int m = mfix[p];
+    pc0[p] = m == 0 ? T(1.0 / 6.0) : m == 1 ? T(2.0 / 3.0) : m == 2 ? T(1.0 / 6.0) : T(0);
+    pc1[p] = m == 0 ? T(-0.5) : m == 1 ? T(0) : m == 2 ? T(0.5) : T(0);
+    pc2[p] = m == 0 ? T(0.5) : m == 1 ? T(-1) : m == 2 ? T(0.5) : T(0);
+    pc3[p] = m == 0 ? T(-1.0 / 6.0) : m == 1 ? T(0.5) : m == 2 ? T(-0.5) : T(1.0 / 6.0);
+  }
 
   // one run per thread when TPP == 1 (runs_per_item == ngroups): which lanes hold one
-  const unsigned has_run_mask = __ballot_sync(0xffffffffu, it.run_lo + group < it.run_hi);
-  for (int rr = it.run_lo + group; rr < it.run_hi; rr += ngroups) {
-    const int r = run_order[rr];
-    const int i0 = run_begin[r], i1 = run_begin[r + 1];
-    const unsigned long long pc = run_cell[r];
+  const unsigned has_run_mask = __ballot_sync(0xffffffffu, group < nr);
+  for (int e = group; e < nr; e += ngroups) {
+    const unsigned span = s_span[e], pc = s_cell[e];
+    const int i0 = pbeg + (int)(span & 0xFFFFu), i1 = pbeg + (int)(span >> 16);
     T tsh[P];
     int base = 0;
 #pragma unroll
     for (int p = 0; p < P; ++p) {
-      const int c = (int)((pc >> (12 * p)) & 0xFFFull);
-      int o = c - it.c0[p];
+      int o = (int)((pc >> (CB * p)) & CMASK);
+      const int c = it.c0[p] + o;
       if (p < F) o += mfix[p];
       base += o * geom.Es[p];
-      tsh[p] = T(geom.lo[p] * geom.inv_h[p] + (double)c);   // t = x * inv - (lo * inv + c)
+      tsh[p] = loinv[p] + T(c);   // t = x * inv - (lo * inv + c)
     }
     const int e0 = R >= 3 ? geom.Es[P - 3] : 0;
     const int e1 = R >= 2 ? geom.Es[P - 2] : 0;
@@ -156,6 +192,7 @@ k_point(const WorkItem* __restrict__ items, const int* __restrict__ run_begin,
 
     for (int i = i0; i < i1; ++i) {
       T bv[P][4];
+      T fixw = T(1);
       if (PRE) {
         const double2* q = reinterpret_cast<const double2*>(pre + (long long)i * (4 * P));
 #pragma unroll
@@ -166,24 +203,33 @@ k_point(const WorkItem* __restrict__ items, const int* __restrict__ run_begin,
           bv[p][2] = T(b.x);
           bv[p][3] = T(b.y);
         }
+#pragma unroll
+        for (int p = 0; p < F; ++p) {   // select without dynamic register indexing
+          const int m = mfix[p];
+          fixw *= m == 0 ? bv[p][0] : m == 1 ? bv[p][1] : m == 2 ? bv[p][2] : bv[p][3];
+        }
       } else {
 #pragma unroll
         for (int p = 0; p < P; ++p) {
           const T xp = T(xsh[p * npts + (i - pbeg)]);
           const T t = fma(xp, inv[p], -tsh[p]);
-          cubic_basis(t, bv[p]);
-          if (MODE == PT_DIAG) {
+          if (ONEPIECE && p < F) {
+            const int q = ONEPIECE ? p : 0;
+            T b = fma(fma(fma(pc3[q], t, pc2[q]), t, pc1[q]), t, pc0[q]);
+            if (MODE == PT_DIAG) b *= b;
+            fixw *= b;
+          } else {
+            cubic_basis(t, bv[p]);
+            if (MODE == PT_DIAG) {
 #pragma unroll
-            for (int m = 0; m < 4; ++m) bv[p][m] *= bv[p][m];
+              for (int m = 0; m < 4; ++m) bv[p][m] *= bv[p][m];
+            }
+            if (!ONEPIECE && p < F) {   // select without dynamic register indexing
+              const int m = mfix[p];
+              fixw *= m == 0 ? bv[p][0] : m == 1 ? bv[p][1] : m == 2 ? bv[p][2] : bv[p][3];
+            }
           }
         }
-      }
-      T fixw = T(1);
-#pragma unroll
-      for (int p = 0; p < F; ++p) {   // select without dynamic register indexing
-        const int m = mfix[p];
-        const T b = m == 0 ? bv[p][0] : m == 1 ? bv[p][1] : m == 2 ? bv[p][2] : bv[p][3];
-        fixw *= b;
       }
       T s;
       if (MODE == PT_APPLY) {
@@ -262,7 +308,7 @@ k_point(const WorkItem* __restrict__ items, const int* __restrict__ run_begin,
       // Coarse levels put a whole warp's runs in one cell: reduce the 64 sums
       // across the warp first (reduce-scatter; lane l ends with the totals of
       // coefficients 2l and 2l+1) instead of 32-way conflicting atomics.
-      const unsigned long long pc0 = __shfl_sync(0xffffffffu, pc, 0);
+      const unsigned pc0 = __shfl_sync(0xffffffffu, pc, 0);
       if (__all_sync(0xffffffffu, pc == pc0)) {
         const int lane = threadIdx.x & 31;
 #pragma unroll
@@ -335,10 +381,14 @@ int launch_point(sps_plan* pl, const Level& L, const T* v, T* u, cudaStream_t st
   // patch accumulator (+ patch of v) + staged coordinates of at most runs_per_item * RUN_MAX points
   const size_t pts = (size_t)runs_per_item(pl->P) * RUN_MAX;
   const size_t smem = (size_t)(MODE == PT_APPLY ? 2 : 1) * L.geom.patch * sizeof(T) + pts * P * sizeof(CT) + 16;
+  if (smem > POINT_SMEM_MAX) {
+    set_error("tile too large for the point operator's shared memory");
+    return SPS_EINVAL;
+  }
   static bool attr_set = false;
   if (!attr_set) {
     SPS_CUDA(cudaFuncSetAttribute(k_point<P, T, CT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  160 * 1024));
+                                  (int)POINT_SMEM_MAX));
     attr_set = true;
   }
   const bool timed = MODE == PT_APPLY && g_prof.active && g_prof.used < PROFILE_MAX;
@@ -349,7 +399,7 @@ int launch_point(sps_plan* pl, const Level& L, const T* v, T* u, cudaStream_t st
       static bool attr_pre = false;
       if (!attr_pre) {
         SPS_CUDA(cudaFuncSetAttribute(k_point<P, T, CT, MODE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      160 * 1024));
+                                      (int)POINT_SMEM_MAX));
         attr_pre = true;
       }
       const size_t smem_pre = (size_t)2 * L.geom.patch * sizeof(T) + 16;
@@ -360,15 +410,23 @@ int launch_point(sps_plan* pl, const Level& L, const T* v, T* u, cudaStream_t st
       return SPS_OK;
     }
   }
-  if constexpr (sizeof(T) == 4 && P == 3) {
-    static bool attr_r2 = false;
-    if (!attr_r2) {
-      SPS_CUDA(cudaFuncSetAttribute(k_point<P, T, CT, MODE, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    160 * 1024));
-      attr_r2 = true;
+  // FP32: two register layouts per run -- R = 2 dimensions in a lane's
+  // registers (4^(P-2) lanes per run, 16 accumulators each) or R = 3
+  // (4^(P-3) lanes, 64 accumulators).  P = 3 defaults to R = 2 (more resident
+  // warps); the autotuner may pick either for the apply of P = 3 and P = 4.
+  constexpr bool TWO_LAYOUTS = sizeof(T) == 4 && (P == 3 || (P == 4 && MODE == PT_APPLY));
+  const int rsel = L.lanes_r ? L.lanes_r : (P == 3 ? 2 : 3);
+  if (TWO_LAYOUTS && (rsel == 2 || (P == 3 && MODE != PT_APPLY))) {
+    if constexpr (TWO_LAYOUTS) {
+      static bool attr_r2 = false;
+      if (!attr_r2) {
+        SPS_CUDA(cudaFuncSetAttribute(k_point<P, T, CT, MODE, false, 2>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)POINT_SMEM_MAX));
+        attr_r2 = true;
+      }
+      k_point<P, T, CT, MODE, false, 2><<<L.nitems, POINT_THREADS, smem, st>>>(
+          L.items, L.run_begin, L.run_cell, L.run_order, xs, pl->n, pl->y_sorted, v, u, L.geom);
     }
-    k_point<P, T, CT, MODE, false, 2><<<L.nitems, POINT_THREADS, smem, st>>>(
-        L.items, L.run_begin, L.run_cell, L.run_order, xs, pl->n, pl->y_sorted, v, u, L.geom);
   } else {
     k_point<P, T, CT, MODE><<<L.nitems, POINT_THREADS, smem, st>>>(L.items, L.run_begin, L.run_cell, L.run_order,
                                                                    xs, pl->n, pl->y_sorted, v, u, L.geom);
@@ -391,6 +449,13 @@ int dispatch_mode(sps_plan* pl, const Level& L, int mode, const T* v, T* u, cuda
 }
 
 }  // namespace
+
+size_t point_apply_smem(const sps_plan* pl, const LevelGeom& G, bool fp32) {
+  const size_t t = fp32 ? 4 : 8;
+  const size_t ct = (fp32 || pl->dtype == SPS_F32) ? 4 : 8;
+  const size_t pts = (size_t)runs_per_item(pl->P) * RUN_MAX;
+  return 2 * (size_t)G.patch * t + pts * pl->P * ct + 16;   // the FP64 basis-value path needs less
+}
 
 template <typename T>
 int point_op(sps_plan* pl, int g, int mode, const T* v, T* u, cudaStream_t st) {

@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <vector>
 #include <cmath>
 
 #include "sps_internal.h"
@@ -278,6 +279,18 @@ __global__ void k_sort_item_runs(const WorkItem* __restrict__ items, const int* 
   if (t < nr) run_order[it.run_lo + t] = it.run_lo + (int)(key[t] & 0xFFFFF);
 }
 
+// Point count of every work item.
+__global__ void k_item_npts(const WorkItem* __restrict__ items, const int* __restrict__ run_begin, int nitems,
+                            unsigned int* __restrict__ npts) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nitems; k += gridDim.x * blockDim.x)
+    npts[k] = (unsigned)(run_begin[items[k].run_hi] - run_begin[items[k].run_lo]);
+}
+
+__global__ void k_permute_items(const WorkItem* __restrict__ in, const unsigned int* __restrict__ perm, int nitems,
+                                WorkItem* __restrict__ out) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nitems; k += gridDim.x * blockDim.x) out[k] = in[perm[k]];
+}
+
 int ensure_seg(sps_plan* pl, long long need) {
   if (pl->seg_cap >= need) return SPS_OK;
   if (pl->seg_tmp) cudaFree(pl->seg_tmp);
@@ -443,6 +456,28 @@ int build_level_work(sps_plan* pl, int g, cudaStream_t st) {
   if (nitems > 0) {
     k_sort_item_runs<<<nitems, 128, 0, st>>>(L.items, L.run_begin, L.run_order);
     SPS_CHECK_LAUNCH("sort item runs");
+  }
+  if (nitems > 1) {
+    // Items in decreasing order of their point counts: CTAs start roughly in
+    // block order, so the large items run in the first wave and the small
+    // ones fill the tail (longest-processing-time-first scheduling).
+    const long long item_words = (long long)((sizeof(WorkItem) + 3) / 4) * nitems;
+    if ((e = ensure_seg(pl, 2LL * nitems + item_words))) return e;
+    unsigned int* npts = (unsigned int*)pl->seg_tmp;
+    unsigned int* perm = npts + nitems;
+    WorkItem* tmp = reinterpret_cast<WorkItem*>(perm + nitems);
+    k_item_npts<<<grid_blocks(nitems, 256), 256, 0, st>>>(L.items, L.run_begin, (int)nitems, npts);
+    SPS_CHECK_LAUNCH("item sizes");
+    std::vector<unsigned int> h(nitems), order(nitems);
+    SPS_CUDA(cudaMemcpyAsync(h.data(), npts, sizeof(unsigned int) * nitems, cudaMemcpyDeviceToHost, st));
+    SPS_CUDA(cudaStreamSynchronize(st));
+    for (unsigned int k = 0; k < nitems; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](unsigned a, unsigned b) { return h[a] > h[b]; });
+    SPS_CUDA(cudaMemcpyAsync(perm, order.data(), sizeof(unsigned int) * nitems, cudaMemcpyHostToDevice, st));
+    k_permute_items<<<grid_blocks(nitems, 256), 256, 0, st>>>(L.items, perm, (int)nitems, tmp);
+    SPS_CHECK_LAUNCH("item order");
+    SPS_CUDA(cudaMemcpyAsync(L.items, tmp, sizeof(WorkItem) * nitems, cudaMemcpyDeviceToDevice, st));
+    SPS_CUDA(cudaStreamSynchronize(st));   // `order` is a host buffer of this frame
   }
   return SPS_OK;
 }

@@ -78,6 +78,9 @@ struct Level {
   // FP64 matrix-free levels: basis values of every point, [point][dim][m]
   double* pre = nullptr;
   long long pre_cap = 0;
+  // FP32 apply of the point operator: dimensions held in a lane's registers
+  // (2: 4^(P-2) lanes per run; 3: 4^(P-3) lanes per run; 0: the default for P)
+  int lanes_r = 0;
   LevelVecs<double> d;
   LevelVecs<float> f;
 };
@@ -92,6 +95,7 @@ struct sps_plan {
   sps_options opt;
   int device = 0;
   int Lbits = 1;            // bits per dimension of the Morton key
+  bool tuned = false;       // the autotuner has chosen the levels' launch shapes
   sps::Level lev[sps::MAXL];
   // points (sorted)
   long long n = 0, n_cap = 0;
@@ -151,6 +155,12 @@ int cuda_fail(cudaError_t e, const char* what);
     cudaError_t _e = (call);                             \
     if (_e != cudaSuccess) return sps::cuda_fail(_e, #call); \
   } while (0)
+// propagate a non-OK status code
+#define SPS_TRY(x)                   \
+  do {                               \
+    int _r = (x);                    \
+    if (_r != SPS_OK) return _r;     \
+  } while (0)
 // every kernel launch is followed by this check, which also counts the launch
 void count_launches(unsigned long long k);
 #define SPS_CHECK_LAUNCH(what)  \
@@ -167,6 +177,9 @@ int build_level_work(sps_plan* pl, int g, cudaStream_t st);
 
 // ---- point_op.cu ----
 enum PointMode { PT_APPLY = 0, PT_DIAG = 1, PT_RHS = 2 };
+// dynamic shared memory of one apply launch on a level with this geometry
+size_t point_apply_smem(const sps_plan* pl, const LevelGeom& G, bool fp32);
+constexpr size_t POINT_SMEM_MAX = 160 * 1024;   // opt-in dynamic shared memory of k_point
 template <typename T>
 int point_op(sps_plan* pl, int g, int mode, const T* v, T* u, cudaStream_t st);
 int basis_precompute(sps_plan* pl, int g, cudaStream_t st);
@@ -176,6 +189,12 @@ bool profile_active();
 int profile_mark();
 void profile_capture_end(int first, int last);
 int profile_harvest(int first, int last);
+
+// ---- api.cu ----
+void level_tile(LevelGeom& G, int ts);   // tile side ts: patch extents, strides and size
+
+// ---- tune.cu ----
+int autotune(sps_plan* pl, cudaStream_t st);
 
 // ---- grid_ops.cu ----
 template <typename T>

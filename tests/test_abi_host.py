@@ -43,8 +43,9 @@ def test_struct_layouts_match_header(B):
 #include <stddef.h>
 #include "sps.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu\n", sizeof(sps_options), offsetof(sps_options, replace_ratio),
-         offsetof(sps_options, precondition), sizeof(sps_result), offsetof(sps_result, solve_ms));
+  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(sps_options), offsetof(sps_options, replace_ratio),
+         offsetof(sps_options, precondition), offsetof(sps_options, lanes_r), sizeof(sps_result),
+         offsetof(sps_result, solve_ms));
   return 0;
 }
 '''
@@ -55,12 +56,13 @@ int main(void) {
         subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
         vals = [int(v) for v in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
     assert vals == [C.sizeof(B.sps_options), B.sps_options.replace_ratio.offset, B.sps_options.precondition.offset,
-                    C.sizeof(B.sps_result), B.sps_result.solve_ms.offset]
+                    B.sps_options.lanes_r.offset, C.sizeof(B.sps_result), B.sps_result.solve_ms.offset]
 
 
 def test_defaults(B):
     o = B.sps_default_options()
     assert (o.precision, o.nu1, o.nu2, o.omega, o.max_iter) == (B.SPS_PREC_FP64, 1, 1, 0.0, 20000)
+    assert (o.hybrid, o.graphs, o.precondition, o.autotune, o.lanes_r) == (1, 1, 1, 0, 0)
 
 
 @pytest.mark.parametrize("args", [
@@ -93,4 +95,15 @@ def test_null_handles(B):
     assert B.lib().sps_destroy(None) == B.SPS_OK
     assert B.lib().sps_solve(None, None, 0, 1e-8, None, None) == B.SPS_EINVAL
     assert B.lib().sps_set_points(None, 10, None, None, 1, 0, None) == B.SPS_EINVAL
+    assert B.lib().sps_get_tuning(None, 1, None, None) == B.SPS_EINVAL
     assert B.lib().sps_launch_count(None) == B.SPS_EINVAL
+
+
+@pytest.mark.parametrize("field,value", [("autotune", 2), ("lanes_r", 1), ("lanes_r", 4), ("tile", 3)])
+def test_plan_create_rejects_bad_options(B, field, value):
+    o = B.sps_default_options()
+    setattr(o, field, value)
+    h = C.c_void_p()
+    iv = (C.c_int * 2)(8, 8)
+    assert B.lib().sps_plan_create(C.byref(h), 2, 3, iv, None, None, 2, 1e-3, C.byref(o)) == B.SPS_EINVAL
+    assert h.value is None
