@@ -33,7 +33,7 @@ import numpy as np  # noqa: E402
 import workloads as W  # noqa: E402
 
 METRIC = "MG-PCG solves/s & operator Gpoint-applies/s at rel.res 1e-8; p50/p99 vs plain FP64"
-POINT_F64_TRAFFIC_BYTES = 101.673472e6 + 3.166464e6   # ncu dram__bytes_read.sum + dram__bytes_write.sum
+POINT_F64_TRAFFIC_BYTES = None   # ncu dram__bytes_read.sum + dram__bytes_write.sum of the current kernel
 
 
 def make_problem(name: str, n: int | None):
@@ -192,7 +192,7 @@ def run_ours(args, pr):
     x_d = torch.from_numpy(np.ascontiguousarray(pr.x)).to(dev)
     y_d = torch.from_numpy(np.ascontiguousarray(pr.y)).to(dev)
     prec = B.SPS_PREC_MIXED if mixed else B.SPS_PREC_FP64
-    plan = B.Plan(pr.P, pr.intervals, pr.levels, pr.lam, pr.lo, pr.hi, precision=prec)
+    plan = B.Plan(pr.P, pr.intervals, pr.levels, pr.lam, pr.lo, pr.hi, precision=prec, autotune=1)
     coef = torch.zeros(plan.K, dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 129 MB L2
 
@@ -267,6 +267,7 @@ def run_ours(args, pr):
     # DRAM bytes (read + write) of one FP64 apply-mode launch on this workload, from one ncu
     # capture of the current kernel (profiles/k_point_fp64_p3_n64_1e6pts.md); None for others
     traffic = POINT_F64_TRAFFIC_BYTES if (fp64_kernel and pr.name == "scale" and pr.n == 1_000_000) else None
+    tuning = [list(B.sps_get_tuning(plan.h, g)) for g in range(1, pr.levels + 1)]
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": "k_point (apply mode), %s" % ("FP64" if fp64_kernel else "FP32/FP64 mix"),
                 "flops_per_launch": flops_launch, "avg_launch_ms": avg_ms, "launches": point_launches,
@@ -281,7 +282,7 @@ def run_ours(args, pr):
             "iterations": res.iterations, "rel_res_true": res.rel_res_true, "fp64_applies": res.fp64_applies,
             "operator_gpoint_applies_per_s": {"fp64_apply": pr.n / (apply64 * 1e-3) / 1e9,
                                               "fp64_point_only": pr.n / (point64 * 1e-3) / 1e9},
-            "roofline": roofline, "clocks": clk, "gpu_launches": launches, "step_ms": step_ms}
+            "point_launch_shape": tuning, "roofline": roofline, "clocks": clk, "gpu_launches": launches, "step_ms": step_ms}
 
     if not mixed:
         point32 = time_apply(lambda h, g, v, u: B.sps_point_apply(h, g, B.SPS_PREC_MIXED, v, u))
@@ -289,7 +290,8 @@ def run_ours(args, pr):
         line["operator_gpoint_applies_per_s"]["fp32_apply_incl_casts"] = pr.n / (apply32 * 1e-3) / 1e9
         line["operator_gpoint_applies_per_s"]["fp32_point_incl_casts"] = pr.n / (point32 * 1e-3) / 1e9
         # the mixed-precision solve of the same workload, beside the plain FP64 one
-        with B.Plan(pr.P, pr.intervals, pr.levels, pr.lam, pr.lo, pr.hi, precision=B.SPS_PREC_MIXED) as pm:
+        with B.Plan(pr.P, pr.intervals, pr.levels, pr.lam, pr.lo, pr.hi, precision=B.SPS_PREC_MIXED,
+                    autotune=1) as pm:
             cm = torch.zeros(plan.K, dtype=torch.float64, device=dev)
             for _ in range(1):
                 pm.set_points(x_d, y_d)
@@ -354,19 +356,50 @@ def run_apply_only(args, pr):
     x_d = torch.from_numpy(np.ascontiguousarray(pr.x)).cuda()
     y_d = torch.from_numpy(np.ascontiguousarray(pr.y)).cuda()
     out = {"workload": workload_desc(pr)}
-    with B.Plan(pr.P, pr.intervals, pr.levels, pr.lam, pr.lo, pr.hi) as plan:
-        plan.set_points(x_d, y_d)
-        v = torch.randn(plan.K, dtype=torch.float64, device="cuda")
-        u = torch.zeros_like(v)
-        for prec, name in ((B.SPS_PREC_FP64, "fp64"), (B.SPS_PREC_MIXED, "fp32")):
+    if args.sweep:
+        # every launch shape of the finest level's point operator (tile side, FP32 lane layout)
+        ts0 = {1: 256, 2: 32, 3: 8, 4: 4, 5: 2}[pr.P]
+        rows = []
+        for ts in (ts0 // 2, ts0, ts0 * 2):
+            for lanes in ((2, 3) if pr.P in (3, 4) else (0,)):
+                try:
+                    with B.Plan(pr.P, pr.intervals, pr.levels, pr.lam, pr.lo, pr.hi, tile=ts, lanes_r=lanes) as plan:
+                        plan.set_points(x_d, y_d)
+                        v = torch.randn(plan.K, dtype=torch.float64, device="cuda")
+                        u = torch.zeros_like(v)
+                        row = {"tile": ts, "lanes_r": lanes}
+                        for prec, name in ((B.SPS_PREC_FP64, "fp64"), (B.SPS_PREC_MIXED, "fp32")):
+                            B.sps_point_apply(plan.h, pr.levels, prec, v, u)
+                            torch.cuda.synchronize()
+                            B.sps_profile_begin()
+                            for _ in range(args.reps):
+                                B.sps_point_apply(plan.h, pr.levels, prec, v, u)
+                            torch.cuda.synchronize()
+                            ms, cnt = B.sps_profile_end()
+                            row[name + "_ms"] = ms / max(cnt, 1)
+                        rows.append(row)
+                except B.SpsError as e:
+                    rows.append({"tile": ts, "lanes_r": lanes, "error": str(e)})
+        out["sweep"] = rows
+        print(json.dumps(out), flush=True)
+        return
+    # the plans of the bench's FP64 and mixed solves (autotuned launch shapes), FP64 first
+    for prec, name in ((B.SPS_PREC_FP64, "fp64"), (B.SPS_PREC_MIXED, "fp32")):
+        with B.Plan(pr.P, pr.intervals, pr.levels, pr.lam, pr.lo, pr.hi, precision=prec, autotune=1) as plan:
+            plan.set_points(x_d, y_d)
+            v = torch.randn(plan.K, dtype=torch.float64, device="cuda")
+            u = torch.zeros_like(v)
             B.sps_point_apply(plan.h, pr.levels, prec, v, u)
             torch.cuda.synchronize()
             B.sps_profile_begin()
+            torch.cuda.profiler.start()   # profiler capture range (ncu --profile-from-start off)
             for _ in range(args.reps):
                 B.sps_point_apply(plan.h, pr.levels, prec, v, u)
             torch.cuda.synchronize()
+            torch.cuda.profiler.stop()
             ms, cnt = B.sps_profile_end()
             out[name + "_ms_per_launch"] = ms / max(cnt, 1)
+            out[name + "_launch_shape"] = list(B.sps_get_tuning(plan.h, pr.levels))
     print(json.dumps(out), flush=True)
 
 
@@ -499,8 +532,15 @@ def run_batched(args):
 
 
 def run_serving(args):
-    """Poisson request trace through the continuous-batching server, then the
-    same requests one at a time with the plain FP64 solver."""
+    """Poisson request trace through the continuous-batching server, then a
+    sample of the same requests one at a time with the plain FP64 solver.
+
+    Every request is solved to --serve-tol with at most --serve-max-iter outer
+    iterations (requests that hit the cap are counted as not converged and
+    reported).  The plain-FP64 comparison runs the first --serve-seq-sample
+    requests of the trace (same arrival times) through the server, and then
+    through a one-slot server with the plain FP64 solver; both report solves/s
+    and p50/p99 latency on exactly those requests."""
     import torch  # noqa: F401
 
     from paper_1901_00654_gb300 import binding as B
@@ -508,7 +548,7 @@ def run_serving(args):
     from paper_1901_00654_gb300 import serving
     libbuild.build_library()
     trace = W.serving_trace(count=args.serve_count, n_hi=args.serve_n_hi)
-    srv = serving.Server(slots=args.slots, tol=args.serve_tol)
+    srv = serving.Server(slots=args.slots, tol=args.serve_tol, max_iter=args.serve_max_iter)
     try:
         warm = W.serving_trace(seed=99, count=4, n_hi=2e4, P_choices=(2, 3))
         srv.run(warm, time_scale=0.0)
@@ -516,20 +556,36 @@ def run_serving(args):
     finally:
         srv.close()
     mixed = stats.summary()
-    seq = serving.Server(slots=1, precision=B.SPS_PREC_FP64, tol=args.serve_tol)
+    by_p = {}
+    for c, rq in zip(stats.completed, trace):
+        d = by_p.setdefault(str(rq.problem.P), {"requests": 0, "converged": 0, "iterations": []})
+        d["requests"] += 1
+        d["converged"] += int(c.status == B.SPS_OK)
+        d["iterations"].append(int(c.result.iterations))
+    for d in by_p.values():
+        d["iterations_median"] = float(np.median(d.pop("iterations")))
+    # the same sub-trace (first requests, same arrival times) served, then one at a time in plain FP64
+    sample = trace[:max(1, min(args.serve_seq_sample, len(trace)))]
+    srv = serving.Server(slots=args.slots, tol=args.serve_tol, max_iter=args.serve_max_iter)
     try:
-        sstats = seq.run(trace)
+        served_sub = srv.run(sample).summary()
+    finally:
+        srv.close()
+    seq = serving.Server(slots=1, precision=B.SPS_PREC_FP64, tol=args.serve_tol, max_iter=args.serve_max_iter)
+    try:
+        plain = seq.run(sample).summary()
     finally:
         seq.close()
-    plain = sstats.summary()
     line = {"metric": METRIC, "value": mixed["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
             "steps": len(trace), "warmup": 4, "ms_per_step": 1e3 / max(mixed["solves_per_s"], 1e-12),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
             "data": "synthetic",
             "config": {"workload": "serving: %d Poisson requests at 200/s, P in {2,3,4,5}, n log-uniform [1e4,%g], "
-                                   "tol %g, %d slots, 120 GB budget" % (len(trace), args.serve_n_hi, args.serve_tol,
-                                                                       args.slots)},
-            "served": mixed, "sequential_plain_fp64": plain}
+                                   "tol %g, at most %d iterations, %d slots, 120 GB budget"
+                                   % (len(trace), args.serve_n_hi, args.serve_tol, args.serve_max_iter, args.slots)},
+            "served": mixed, "served_by_P": by_p,
+            "same_requests": {"requests": len(sample), "what": "first %d requests of the trace, same arrivals"
+                              % len(sample), "served": served_sub, "sequential_plain_fp64": plain}}
     print(json.dumps(line), flush=True)
 
 
@@ -547,11 +603,16 @@ def main():
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--batch-tol", type=float, default=1e-8)
     ap.add_argument("--seq-sample", type=int, default=32)
-    ap.add_argument("--serve-count", type=int, default=200)
+    ap.add_argument("--serve-count", type=int, default=48)
     ap.add_argument("--serve-n-hi", type=float, default=2e6)
     ap.add_argument("--serve-tol", type=float, default=1e-6)
+    ap.add_argument("--serve-max-iter", type=int, default=1500)
+    ap.add_argument("--serve-seq-sample", type=int, default=6)
+    ap.add_argument("--sweep", action="store_true", help="with --apply-only: every tile side and lane layout")
     ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--n", type=int, default=None, help="override the number of points")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default=None,
+                    help="override the workload's solver precision (--launch-profile, --apply-only)")
     ap.add_argument("--ref-sample", type=int, default=200_000)
     ap.add_argument("--ref-iters", type=int, default=12, help="iterations assumed by the reference arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -563,6 +624,8 @@ def main():
     if args.config == "paper":
         return run_paper(args)
     pr = make_problem(args.config, args.n)
+    if args.precision:
+        pr.precision = args.precision
     if args.apply_only:
         return run_apply_only(args, pr)
     if args.launch_profile:

@@ -179,7 +179,10 @@ __device__ __forceinline__ void deinterleave(unsigned long long id, int P, int b
     }
 }
 
-// Runs per level cell: ceil(points / RUN_MAX).  cnt has ncell + 1 entries.
+// Runs per level cell: ceil(points / RUN_MAX), of balanced lengths (a cell
+// of 17 points gives runs of 9 and 8, not 16 and 1), so that the lanes of a
+// warp, which walk runs of similar rank, finish together.  cnt has ncell + 1
+// entries.
 __global__ void k_cell_runs(const unsigned long long* __restrict__ keys, long long n, long long ncell,
                             int sh, unsigned int* __restrict__ cnt) {
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c <= ncell;
@@ -200,12 +203,14 @@ __global__ void k_fill_runs(const unsigned long long* __restrict__ keys, long lo
     unsigned int o0 = off[c], o1 = off[c + 1];
     if (o0 == o1) continue;
     long long a = lower_bound_key(keys, n, (unsigned long long)c << sh);
+    const long long m = lower_bound_key(keys, n, (unsigned long long)(c + 1) << sh) - a;
+    const long long k = o1 - o0;   // ceil(m / RUN_MAX) runs of floor(m/k) or ceil(m/k) points
     int cc[MAXP];
     deinterleave((unsigned long long)c, P, cbits, cc);
     unsigned long long packed = 0;
     for (int p = 0; p < P; ++p) packed |= (unsigned long long)cc[p] << (12 * p);
     for (unsigned int r = o0; r < o1; ++r) {
-      run_begin[r] = (int)(a + (long long)(r - o0) * RUN_MAX);
+      run_begin[r] = (int)(a + (long long)(r - o0) * m / k);
       run_cell[r] = packed;
     }
   }
