@@ -33,7 +33,9 @@ import numpy as np  # noqa: E402
 import workloads as W  # noqa: E402
 
 METRIC = "MG-PCG solves/s & operator Gpoint-applies/s at rel.res 1e-8; p50/p99 vs plain FP64"
-POINT_F64_TRAFFIC_BYTES = None   # ncu dram__bytes_read.sum + dram__bytes_write.sum of the current kernel
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of one FP64 apply launch on the 64^3,
+# 10^6-point workload at tile side 16 (profiles/k_point_fp64_p3_n64_1e6pts.md)
+POINT_F64_TRAFFIC_BYTES = 101.887744e6 + 3.518976e6
 
 
 def make_problem(name: str, n: int | None):
@@ -266,8 +268,9 @@ def run_ours(args, pr):
     peak = 2.0 * fma_rate / 1e12
     # DRAM bytes (read + write) of one FP64 apply-mode launch on this workload, from one ncu
     # capture of the current kernel (profiles/k_point_fp64_p3_n64_1e6pts.md); None for others
-    traffic = POINT_F64_TRAFFIC_BYTES if (fp64_kernel and pr.name == "scale" and pr.n == 1_000_000) else None
     tuning = [list(B.sps_get_tuning(plan.h, g)) for g in range(1, pr.levels + 1)]
+    traffic = POINT_F64_TRAFFIC_BYTES if (fp64_kernel and pr.name == "scale" and pr.n == 1_000_000
+                                          and tuning[-1] == [16, 0]) else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": "k_point (apply mode), %s" % ("FP64" if fp64_kernel else "FP32/FP64 mix"),
                 "flops_per_launch": flops_launch, "avg_launch_ms": avg_ms, "launches": point_launches,

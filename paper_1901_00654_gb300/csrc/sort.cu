@@ -184,18 +184,20 @@ __device__ __forceinline__ void deinterleave(unsigned long long id, int P, int b
 // warp, which walk runs of similar rank, finish together.  cnt has ncell + 1
 // entries.
 __global__ void k_cell_runs(const unsigned long long* __restrict__ keys, long long n, long long ncell,
-                            int sh, unsigned int* __restrict__ cnt) {
+                            int sh, unsigned int* __restrict__ cnt, unsigned int* __restrict__ pts) {
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c <= ncell;
        c += (long long)gridDim.x * blockDim.x) {
     if (c == ncell) { cnt[c] = 0; continue; }
     long long a = lower_bound_key(keys, n, (unsigned long long)c << sh);
     long long b = lower_bound_key(keys, n, (unsigned long long)(c + 1) << sh);
     cnt[c] = (unsigned int)((b - a + RUN_MAX - 1) / RUN_MAX);
+    pts[c] = (unsigned int)(b - a);
   }
 }
 
 __global__ void k_fill_runs(const unsigned long long* __restrict__ keys, long long n, long long ncell,
                             int sh, int P, int cbits, const unsigned int* __restrict__ off,
+                            const unsigned int* __restrict__ pts,
                             int* __restrict__ run_begin, unsigned long long* __restrict__ run_cell,
                             long long nruns) {
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
@@ -203,7 +205,7 @@ __global__ void k_fill_runs(const unsigned long long* __restrict__ keys, long lo
     unsigned int o0 = off[c], o1 = off[c + 1];
     if (o0 == o1) continue;
     long long a = lower_bound_key(keys, n, (unsigned long long)c << sh);
-    const long long m = lower_bound_key(keys, n, (unsigned long long)(c + 1) << sh) - a;
+    const long long m = pts[c];
     const long long k = o1 - o0;   // ceil(m / RUN_MAX) runs of floor(m/k) or ceil(m/k) points
     int cc[MAXP];
     deinterleave((unsigned long long)c, P, cbits, cc);
@@ -403,7 +405,8 @@ int build_level_work(sps_plan* pl, int g, cudaStream_t st) {
   if (e) return e;
   unsigned int* run_off = (unsigned int*)pl->seg_tmp;
   unsigned int* item_off = run_off + (ncell + 1);
-  k_cell_runs<<<grid_blocks(ncell + 1, 256), 256, 0, st>>>(pl->keys, pl->n, ncell, sh, run_off);
+  // item_off holds the cells' point counts until the items are built
+  k_cell_runs<<<grid_blocks(ncell + 1, 256), 256, 0, st>>>(pl->keys, pl->n, ncell, sh, run_off, item_off);
   SPS_CHECK_LAUNCH("cell runs");
   if ((e = scan_u32(run_off, ncell + 1, st))) return e;
   unsigned int nruns = 0;
@@ -427,7 +430,7 @@ int build_level_work(sps_plan* pl, int g, cudaStream_t st) {
     L.run_cap = (int)cap;
   }
   L.nruns = (int)nruns;
-  k_fill_runs<<<grid_blocks(ncell, 256), 256, 0, st>>>(pl->keys, pl->n, ncell, sh, P, cbits, run_off,
+  k_fill_runs<<<grid_blocks(ncell, 256), 256, 0, st>>>(pl->keys, pl->n, ncell, sh, P, cbits, run_off, item_off,
                                                        L.run_begin, L.run_cell, nruns);
   SPS_CHECK_LAUNCH("fill runs");
   // tiles of ts^P level cells
