@@ -99,15 +99,16 @@ typedef struct sps_options {
                               Section 4 (Table 2, Fig. 2) */
     int    autotune;       /* 1: on the plan's first sps_set_points, time the
                               point operator of every matrix-free level with
-                              tile sides ts/2, ts, 2ts (and, in the mixed mode
-                              for P = 3, 4, both lane layouts per run) and keep
+                              tile sides ts/2, ts, 2ts (and, for P = 3, 4, both
+                              lane layouts per run) and keep
                               the fastest; the operator is the same matrix.
                               0 (default): fixed tile side per P */
-    int    lanes_r;        /* FP32 apply of the point operator for P = 3, 4:
+    int    lanes_r;        /* apply of the point operator for P = 3, 4 (FP32,
+                              and FP64 on levels with precomputed basis values):
                               dimensions of a run's (q+1)^P coefficients held in
                               one lane's registers, 2 (4^(P-2) lanes per run,
                               16 sums each) or 3 (4^(P-3) lanes, 64 sums);
-                              0 (default): 2 for P = 3, 3 for P = 4.  Ignored
+                              0 (default): FP32 2 for P = 3, else 3.  Ignored
                               for other P; the autotuner may change it */
 } sps_options;
 

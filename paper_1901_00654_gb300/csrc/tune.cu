@@ -3,9 +3,10 @@
 // The point operator's speed depends on two choices that the data decide: the
 // tile side ts (cells per CTA along each dimension: a larger tile amortises
 // the staging and flush of its (ts+q)^P coefficient patch over more points,
-// a smaller one gives more CTAs and less shared memory per CTA), and, in
-// FP32, how many lanes share one run of points (4^(P-2) lanes holding 16
-// accumulators each, or 4^(P-3) lanes holding 64).  On the first
+// a smaller one gives more CTAs and less shared memory per CTA), and, for
+// P = 3, 4 (FP32, or FP64 from precomputed basis values), how many lanes
+// share one run of points (4^(P-2) lanes holding 16 accumulators each, or
+// 4^(P-3) lanes holding 64).  On the first
 // sps_set_points of a plan with autotune = 1, every matrix-free level that
 // the solve applies is timed with each candidate (CUDA events, the solve's
 // own precision) and keeps the fastest; later set-ups of the plan reuse the
@@ -60,7 +61,8 @@ int tune_level(sps_plan* pl, int g, bool fp32, cudaEvent_t e0, cudaEvent_t e1, c
     LevelGeom G = L.geom;
     level_tile(G, ts);
     if (point_apply_smem(pl, G, fp32) > POINT_SMEM_MAX - 2048) continue;
-    if (fp32 && (P == 3 || P == 4)) {
+    const bool pre = !fp32 && L.pre != nullptr;   // FP64 apply from precomputed basis values
+    if ((fp32 || pre) && (P == 3 || P == 4)) {
       cand.push_back({ts, 2});
       cand.push_back({ts, 3});
     } else {

@@ -26,13 +26,17 @@ def _phi_all(x, lo, hi, intervals, G):
 @pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "P%d" % s[0])
 @pytest.mark.parametrize("lanes_r", [2, 3])
 @pytest.mark.parametrize("tile_scale", [0.5, 1, 2])
-def test_lane_layouts_and_tiles_match_oracle(shape, lanes_r, tile_scale):
+@pytest.mark.parametrize("prec", [B.SPS_PREC_FP64, B.SPS_PREC_MIXED], ids=["fp64", "mixed"])
+def test_lane_layouts_and_tiles_match_oracle(shape, lanes_r, tile_scale, prec):
+    # FP64 plans apply matrix-free levels >= 2 from precomputed basis values (both layouts);
+    # level 1 and the FP32 kernels evaluate the basis from the coordinates
     P, intervals, G, n = shape
     x, y, lo, hi = random_problem(P, intervals, n, seed=300 + P)
     tile = int(TS_DEFAULT[P] * tile_scale)
     phis = _phi_all(x, lo, hi, intervals, G)
     r = np.random.default_rng(5)
-    with B.Plan(P, intervals, G, 1e-3, lo, hi, precision=B.SPS_PREC_MIXED, lanes_r=lanes_r, tile=tile) as pl:
+    tol = FP64_TOL if prec == B.SPS_PREC_FP64 else FP32_TOL
+    with B.Plan(P, intervals, G, 1e-3, lo, hi, precision=prec, lanes_r=lanes_r, tile=tile, hybrid=0) as pl:
         pl.set_points(x, y)
         for g in range(1, G + 1):
             ts, lr = B.sps_get_tuning(pl.h, g)
@@ -40,8 +44,8 @@ def test_lane_layouts_and_tiles_match_oracle(shape, lanes_r, tile_scale):
             Phi = phis[g]
             v = r.standard_normal(Phi.shape[1])
             u = np.zeros_like(v)
-            B.sps_point_apply(pl.h, g, B.SPS_PREC_MIXED, v, u)
-            assert rel_err(u, Phi.T @ (Phi @ v)) < FP32_TOL, (g, rel_err(u, Phi.T @ (Phi @ v)))
+            B.sps_point_apply(pl.h, g, prec, v, u)
+            assert rel_err(u, Phi.T @ (Phi @ v)) < tol, (g, rel_err(u, Phi.T @ (Phi @ v)))
 
 
 @pytest.mark.parametrize("prec", [B.SPS_PREC_FP64, B.SPS_PREC_MIXED])
@@ -58,7 +62,7 @@ def test_autotune_choice_and_solve(prec):
             for g in range(2, G + 1):
                 ts, lr = B.sps_get_tuning(pl.h, g)
                 assert ts in (4, 8, 16)
-                assert lr in ((2, 3) if (autotune and prec == B.SPS_PREC_MIXED) else (0,))
+                assert lr in ((2, 3) if autotune else (0,))
                 Phi = phis[g]
                 v = np.random.default_rng(g).standard_normal(Phi.shape[1])
                 u = np.zeros_like(v)
