@@ -34,8 +34,9 @@ import workloads as W  # noqa: E402
 
 METRIC = "MG-PCG solves/s & operator Gpoint-applies/s at rel.res 1e-8; p50/p99 vs plain FP64"
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one FP64 apply launch on the 64^3,
-# 10^6-point workload at tile side 16 (profiles/k_point_fp64_p3_n64_1e6pts.md)
-POINT_F64_TRAFFIC_BYTES = 101.887744e6 + 3.518976e6
+# 10^6-point workload at tile side 4, four lanes per run (profiles/k_point_fp64_p3_n64_1e6pts.md)
+POINT_F64_TRAFFIC_BYTES = 101.769984e6 + 3.193088e6
+POINT_F64_TRAFFIC_SHAPE = [4, 2]
 
 
 def make_problem(name: str, n: int | None):
@@ -270,7 +271,7 @@ def run_ours(args, pr):
     # capture of the current kernel (profiles/k_point_fp64_p3_n64_1e6pts.md); None for others
     tuning = [list(B.sps_get_tuning(plan.h, g)) for g in range(1, pr.levels + 1)]
     traffic = POINT_F64_TRAFFIC_BYTES if (fp64_kernel and pr.name == "scale" and pr.n == 1_000_000
-                                          and tuning[-1] == [16, 0]) else None
+                                          and tuning[-1] == POINT_F64_TRAFFIC_SHAPE) else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": "k_point (apply mode), %s" % ("FP64" if fp64_kernel else "FP32/FP64 mix"),
                 "flops_per_launch": flops_launch, "avg_launch_ms": avg_ms, "launches": point_launches,
@@ -387,8 +388,10 @@ def run_apply_only(args, pr):
         print(json.dumps(out), flush=True)
         return
     # the plans of the bench's FP64 and mixed solves (autotuned launch shapes), FP64 first
+    # --tile / --lanes-r fix the launch shape (no tuning) so that a profiler sees a known shape
+    shape = dict(tile=args.tile, lanes_r=args.lanes_r, autotune=0) if args.tile else dict(autotune=1)
     for prec, name in ((B.SPS_PREC_FP64, "fp64"), (B.SPS_PREC_MIXED, "fp32")):
-        with B.Plan(pr.P, pr.intervals, pr.levels, pr.lam, pr.lo, pr.hi, precision=prec, autotune=1) as plan:
+        with B.Plan(pr.P, pr.intervals, pr.levels, pr.lam, pr.lo, pr.hi, precision=prec, **shape) as plan:
             plan.set_points(x_d, y_d)
             v = torch.randn(plan.K, dtype=torch.float64, device="cuda")
             u = torch.zeros_like(v)
@@ -420,7 +423,7 @@ def run_launch_profile(args, pr):
     y_d = torch.from_numpy(np.ascontiguousarray(pr.y)).cuda()
     prec = B.SPS_PREC_MIXED if pr.precision == "mixed" else B.SPS_PREC_FP64
     with B.Plan(pr.P, pr.intervals, pr.levels, pr.lam, pr.lo, pr.hi, precision=prec,
-                max_iter=args.profile_iters) as plan:
+                max_iter=args.profile_iters, autotune=1) as plan:
         coef = torch.zeros(plan.K, dtype=torch.float64, device="cuda")
         l0 = B.sps_launch_count()
         B.sps_profile_begin()
@@ -431,6 +434,7 @@ def run_launch_profile(args, pr):
         wall = time.perf_counter() - t0
         pm, pn = B.sps_profile_end()
         print(json.dumps({"workload": workload_desc(pr), "iterations": res.iterations, "launches": B.sps_launch_count() - l0,
+                          "point_launch_shape": [list(B.sps_get_tuning(plan.h, g)) for g in range(1, pr.levels + 1)],
                           "wall_ms": wall * 1e3, "point_apply_ms": pm, "point_apply_launches": pn,
                           "point_apply_share_of_wall": pm / (wall * 1e3)}), flush=True)
 
@@ -612,6 +616,8 @@ def main():
     ap.add_argument("--serve-max-iter", type=int, default=1500)
     ap.add_argument("--serve-seq-sample", type=int, default=6)
     ap.add_argument("--sweep", action="store_true", help="with --apply-only: every tile side and lane layout")
+    ap.add_argument("--tile", type=int, default=0, help="with --apply-only: fixed tile side (no autotuning)")
+    ap.add_argument("--lanes-r", type=int, default=0, help="with --apply-only --tile: fixed lane layout")
     ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--n", type=int, default=None, help="override the number of points")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default=None,

@@ -207,12 +207,14 @@ __global__ void k_fill_runs(const unsigned long long* __restrict__ keys, long lo
     long long a = lower_bound_key(keys, n, (unsigned long long)c << sh);
     const long long m = pts[c];
     const long long k = o1 - o0;   // ceil(m / RUN_MAX) runs of floor(m/k) or ceil(m/k) points
+    const long long len = m / k, extra = m - len * k;   // the first `extra` runs hold one more
     int cc[MAXP];
     deinterleave((unsigned long long)c, P, cbits, cc);
     unsigned long long packed = 0;
     for (int p = 0; p < P; ++p) packed |= (unsigned long long)cc[p] << (12 * p);
     for (unsigned int r = o0; r < o1; ++r) {
-      run_begin[r] = (int)(a + (long long)(r - o0) * m / k);
+      const long long j = r - o0;
+      run_begin[r] = (int)(a + j * len + (j < extra ? j : extra));
       run_cell[r] = packed;
     }
   }
