@@ -174,6 +174,7 @@ def run_ours(args, pr):
 
     from paper_1901_00654_gb300 import binding as B
     from paper_1901_00654_gb300 import build as libbuild
+    from paper_1901_00654_gb300 import replicas
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -232,11 +233,8 @@ def run_ours(args, pr):
     clk = clocks.stop()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = sum(step_ms)
-    t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    max_ms = float(t.item())
-    value = world * args.steps / (max_ms * 1e-3)
+    value, max_s = replicas.job_rate(args.steps, total_ms * 1e-3, world, dev)
+    max_ms = max_s * 1e3
     res = results[-1]
 
     # ---- operator apply throughput on the finest level (FP64 and FP32 kernels)
@@ -331,10 +329,8 @@ def run_ours(args, pr):
         plan.solve(pr.tol, cn)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    line["e2e"] = {"value": world * e2e_steps / float(te.item()), "unit": "solves/s", "steps": e2e_steps,
+    e2e_rate, _ = replicas.job_rate(e2e_steps, e2e_s, world, dev)
+    line["e2e"] = {"value": e2e_rate, "unit": "solves/s", "steps": e2e_steps,
                    "h2d_bytes_per_step": int(xn.nbytes + yn.nbytes), "d2h_bytes_per_step": int(cn.nbytes)}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
