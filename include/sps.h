@@ -187,6 +187,19 @@ SPS_API const char* sps_last_error(void);
 SPS_API int sps_solve_batch(sps_plan* const* plans, int count, double* const* coefs, int mem, double tol,
                             sps_result* results, void* stream);
 
+/* Values s(x_j) = sum_k alpha_k phi_k(x_j) of the spline with coefficients
+ * `coef` at m query points: Algorithm 4 (transposed Khatri-Rao product) with
+ * the query points in place of the data, on the finest grid of the plan
+ * (Sections 2.1, 2.2) -- how a fitted smoothing spline is used to predict.
+ * coef: K_G doubles (the layout of sps_solve); xq: m x P row-major, dtype
+ * SPS_F32 or SPS_F64; out: m doubles; all three in `mem`.  Needs only
+ * sps_plan_create (no points).  A point on x = hi belongs to the last cell.
+ * Errors: SPS_EINVAL; SPS_EDOM if a query point is outside [lo, hi] or not
+ * finite (its value is NaN, the others are evaluated).  m = 0 does nothing.
+ * Synchronises `stream`. */
+SPS_API int sps_evaluate(sps_plan* plan, const double* coef, int64_t m, const void* xq, int dtype, double* out,
+                         int mem, void* stream);
+
 /* Launch shape of level `level`'s point operator (after sps_set_points):
  * tile side in cells and, for the FP32 apply, the dimensions held in one
  * lane's registers (2 or 3; 0 = the default for P).  Not a step of the

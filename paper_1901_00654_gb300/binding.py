@@ -30,7 +30,7 @@ EXPORTED = ["sps_default_options", "sps_plan_create", "sps_set_points", "sps_sol
             "sps_prolong", "sps_restrict", "sps_coarse_solve", "sps_vcycle", "sps_get_sort", "sps_get_omega",
             "sps_set_omega", "sps_probe_fma_rate", "sps_point_apply", "sps_launch_count",
             "sps_profile_begin", "sps_profile_end", "sps_solve_batch", "sps_set_lambda",
-            "sps_penalty_apply_noalloc", "sps_get_tuning"]
+            "sps_penalty_apply_noalloc", "sps_get_tuning", "sps_evaluate"]
 
 
 class sps_options(C.Structure):
@@ -78,6 +78,7 @@ def load(path: str | None = None) -> C.CDLL:
         "sps_get_sort": (I, [P, P, P, I, P]),
         "sps_get_omega": (I, [P, P]),
         "sps_get_tuning": (I, [P, I, P, P]),
+        "sps_evaluate": (I, [P, P, C.c_int64, P, I, P, I, P]),
         "sps_set_omega": (I, [P, P]),
         "sps_probe_fma_rate": (I, [I, C.POINTER(D), P]),
         "sps_point_apply": (I, [P, I, I, P, P, I, P]),
@@ -242,6 +243,20 @@ def sps_point_apply(plan, level, prec, v, u, stream=None):
     _vec_call("sps_point_apply", plan, level, prec, v, u, stream)
 
 
+def sps_evaluate(plan, coef, xq, out, stream=None) -> None:
+    """out[j] = s(xq[j]) of the spline with coefficients coef (finest grid)."""
+    pc, mc = _buf(coef)
+    px, mx = _buf(xq)
+    po, mo = _buf(out)
+    if not (mc == mx == mo):
+        raise ValueError("coef, xq and out must live in the same memory")
+    dt = str(xq.dtype)
+    dtype = SPS_F64 if dt.endswith("float64") else SPS_F32 if dt.endswith("float32") else None
+    if dtype is None:
+        raise TypeError("xq must be float32 or float64")
+    _check(lib().sps_evaluate(plan, pc, xq.shape[0], px, dtype, po, mc, _stream(stream)), "sps_evaluate")
+
+
 def sps_launch_count() -> int:
     c = C.c_uint64()
     _check(lib().sps_launch_count(C.byref(c)), "sps_launch_count")
@@ -352,6 +367,13 @@ class Plan:
             coef = np.zeros(self.K)
         res = sps_solve(self.h, coef, tol, stream, check=check)
         return coef, res
+
+    def evaluate(self, coef, xq, out=None, stream=None):
+        """Values of the spline with coefficients coef at the query points xq."""
+        if out is None:
+            out = np.zeros(xq.shape[0])
+        sps_evaluate(self.h, coef, xq, out, stream)
+        return out
 
     def close(self):
         if self.h:

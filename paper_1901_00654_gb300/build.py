@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB_PATH = os.path.join(LIBDIR, "libsps.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["api.cu", "point_op.cu", "grid_ops.cu", "sort.cu", "batch.cu", "noalloc.cu", "tune.cu"]
+SOURCES = ["api.cu", "point_op.cu", "grid_ops.cu", "sort.cu", "batch.cu", "noalloc.cu", "tune.cu", "evaluate.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-diag-suppress", "177"]

@@ -107,3 +107,19 @@ def test_plan_create_rejects_bad_options(B, field, value):
     iv = (C.c_int * 2)(8, 8)
     assert B.lib().sps_plan_create(C.byref(h), 2, 3, iv, None, None, 2, 1e-3, C.byref(o)) == B.SPS_EINVAL
     assert h.value is None
+
+
+def test_evaluate_rejects_bad_arguments(B):
+    assert B.lib().sps_evaluate(None, None, 0, None, 1, None, 0, None) == B.SPS_EINVAL
+    o = B.sps_default_options()
+    h = C.c_void_p()
+    iv = (C.c_int * 2)(8, 8)
+    # plan creation and argument checks run before any device work
+    if B.lib().sps_plan_create(C.byref(h), 2, 3, iv, None, None, 2, 1e-3, C.byref(o)) != B.SPS_OK:
+        pytest.skip("plan creation needs a GPU here")
+    try:
+        assert B.lib().sps_evaluate(h, None, -1, None, 1, None, 0, None) == B.SPS_EINVAL
+        assert B.lib().sps_evaluate(h, None, 4, None, 1, None, 0, None) == B.SPS_EINVAL
+        assert B.lib().sps_evaluate(h, None, 0, None, 7, None, 0, None) == B.SPS_EINVAL
+    finally:
+        B.lib().sps_destroy(h)
