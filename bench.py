@@ -467,9 +467,18 @@ def run_paper(args):
 
     table2 = {P: run(P, 5) for P in (1, 2, 3, 4)}
     fig2 = {G: run(2, G) for G in (4, 5, 6, 7)}
+    # Table 3 / Fig. 3: condition numbers of A_G and C_MG A_G at P = 2, G = 5 (K = 1225)
+    from paper_1901_00654_gb300 import analysis
+    x, y = W.paper_sigmoid(5, 100_000, 2)
+    with B.Plan(2, [32, 32], 5, lam) as pl:
+        pl.set_points(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda())
+        sp = analysis.spectra(*analysis.operator_matrices(pl, 5))
+    table3 = {"kappa_A": sp["kappa_A"], "kappa_MG_JAC_A": sp["kappa_MA"],
+              "eig_MG_JAC_A_min_max": [float(sp["eig_MA"][0]), float(sp["eig_MA"][-1])],
+              "paper": {"kappa_A": 1933.27, "kappa_MG_JAC_A": 1.82}}
     line = {"workload": "paper Section 4: n=1e5 sigmoid data, lambda=%g, rel.res %g, FP64" % (lam, tol),
             "table2_gpu": table2, "fig2_gpu_P2": fig2,
-            "table2_paper_iterations_cg_mgcg": paper}
+            "table2_paper_iterations_cg_mgcg": paper, "table3_gpu": table3}
     print(json.dumps(line), flush=True)
 
 
