@@ -34,8 +34,9 @@ import workloads as W  # noqa: E402
 
 METRIC = "MG-PCG solves/s & operator Gpoint-applies/s at rel.res 1e-8; p50/p99 vs plain FP64"
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one FP64 apply launch on the 64^3,
-# 10^6-point workload at tile side 4, four lanes per run (profiles/k_point_fp64_p3_n64_1e6pts.md)
-POINT_F64_TRAFFIC_BYTES = 101.769984e6 + 3.193088e6
+# 10^6-point workload at tile side 4, four lanes per run, precomputed basis products
+# (profiles/k_point_fp64_p3_n64_1e6pts.md)
+POINT_F64_TRAFFIC_BYTES = 166.79808e6 + 3.586304e6
 POINT_F64_TRAFFIC_SHAPE = [4, 2]
 
 

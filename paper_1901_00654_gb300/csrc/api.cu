@@ -859,6 +859,7 @@ int sps_destroy(sps_plan* pl) {
     cudaFree(L.st_d);
     cudaFree(L.st_f);
     cudaFree(L.pre);
+    cudaFree(L.pre2);
     cudaFree(L.run_begin);
     cudaFree(L.run_cell);
     cudaFree(L.run_order);
@@ -980,6 +981,16 @@ int sps_set_points(sps_plan* pl, int64_t n, const void* x, const void* y, int dt
         L.pre_cap = 0;
         SPS_TRY(alloc(&L.pre, need));
         L.pre_cap = need;
+      }
+      if (P == 3) {   // products for the four-lane layout
+        const long long need2 = pl->n * (long long)PRE2_STRIDE;
+        if (L.pre2_cap < need2) {
+          cudaFree(L.pre2);
+          L.pre2 = nullptr;
+          L.pre2_cap = 0;
+          SPS_TRY(alloc(&L.pre2, need2));
+          L.pre2_cap = need2;
+        }
       }
       SPS_TRY(basis_precompute(pl, g, st));
     }

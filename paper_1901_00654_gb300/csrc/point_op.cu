@@ -47,16 +47,19 @@ __device__ __forceinline__ void cubic_basis(T t, T* b) {
   b[3] = t2 * (t * T(1.0 / 6.0));
 }
 
-// PRE (FP64 only): the 4P basis values of every point on this level were
+// PRE (FP64 only): 1 -- the 4P basis values of every point on this level were
 // computed once at set-up and are read from `pre` ([point][dimension][m])
 // instead of being re-evaluated from the coordinates in every sweep.  On
 // GB300 an FP64 operation costs about as much as moving 40 bytes from HBM, so
 // streaming 8*4P bytes per point is cheaper than the 12P FP64 operations.
+// 2 (P = 3, four-lane layout) -- per point the 4 pieces of the first dimension
+// and the 16 products of the other two, so each lane's gather and scatter are
+// 16 multiply-adds each with no product formation (160 bytes per point).
 // RR: dimensions held in a lane's registers (0 = min(P, 3)); the FP32
 // kernel for P = 3 uses RR = 2, i.e. four lanes per run with 16 coefficients
 // each, for four times the resident warps of the one-lane layout.
-template <int P, typename T, typename CT, int MODE, bool PRE = false, int RR = 0>
-__global__ void __launch_bounds__(POINT_THREADS, 2)
+template <int P, typename T, typename CT, int MODE, int PRE = 0, int RR = 0>
+__global__ void __launch_bounds__(POINT_THREADS, PRE == 2 ? 5 : 2)
 k_point(const WorkItem* __restrict__ items, const int* __restrict__ run_begin,
         const unsigned long long* __restrict__ run_cell, const int* __restrict__ run_order,
         const CT* __restrict__ xs, long long n,
@@ -191,6 +194,29 @@ k_point(const WorkItem* __restrict__ items, const int* __restrict__ run_begin,
     for (int k = 0; k < NR; ++k) accr[k] = T(0);
 
     for (int i = i0; i < i1; ++i) {
+      if constexpr (PRE == 2 && P == 3 && R == 2 && MODE == PT_APPLY) {
+        // products b2[b] b3[d] precomputed: 16 multiply-adds each way per lane
+        const double* q = pre + (long long)i * PRE2_STRIDE;
+        const T ba = T(q[mfix[0]]);
+        const double2* q2 = reinterpret_cast<const double2*>(q + 4);
+        T pr[16];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const double2 t = __ldg(q2 + k);
+          pr[2 * k] = T(t.x);
+          pr[2 * k + 1] = T(t.y);
+        }
+        T g = T(0);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) g = fma(pr[k], VREG ? vr[VREG ? k : 0] : vp[vidx(k)], g);
+        g *= ba;
+#pragma unroll
+        for (int o = TPP / 2; o >= 1; o >>= 1) g += __shfl_xor_sync(gmask, g, o, TPP);
+        const T w = g * ba;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) accr[k] = fma(w, pr[k], accr[k]);
+        continue;
+      }
       T bv[P][4];
       T fixw = T(1);
       if (PRE) {
@@ -398,7 +424,7 @@ int launch_point(sps_plan* pl, const Level& L, const T* v, T* u, cudaStream_t st
     if (L.pre) {
       static bool attr_pre = false;
       if (!attr_pre) {
-        SPS_CUDA(cudaFuncSetAttribute(k_point<P, T, CT, MODE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        SPS_CUDA(cudaFuncSetAttribute(k_point<P, T, CT, MODE, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)POINT_SMEM_MAX));
         attr_pre = true;
       }
@@ -406,22 +432,37 @@ int launch_point(sps_plan* pl, const Level& L, const T* v, T* u, cudaStream_t st
       // P = 3, 4: the 4^(P-2)-lane layout (16 sums per lane) when chosen: about
       // 10 % more FP64 operations per point, but four times the resident warps
       // and runs of more similar length within a warp
+      if constexpr (P == 3) {
+        if (L.lanes_r == 2 && L.pre2) {   // products of the last two dimensions precomputed
+          static bool attr_pre22 = false;
+          if (!attr_pre22) {
+            SPS_CUDA(cudaFuncSetAttribute(k_point<P, T, CT, MODE, 2, 2>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)POINT_SMEM_MAX));
+            attr_pre22 = true;
+          }
+          k_point<P, T, CT, MODE, 2, 2><<<L.nitems, POINT_THREADS, smem_pre, st>>>(
+              L.items, L.run_begin, L.run_cell, L.run_order, xs, pl->n, pl->y_sorted, v, u, L.geom, L.pre2);
+          SPS_CHECK_LAUNCH("point operator");
+          if (timed) SPS_CUDA(record_event(g_prof.ev[2 * g_prof.used++ + 1], st));
+          return SPS_OK;
+        }
+      }
       if constexpr (P == 3 || P == 4) {
         if (L.lanes_r == 2) {
           static bool attr_pre2 = false;
           if (!attr_pre2) {
-            SPS_CUDA(cudaFuncSetAttribute(k_point<P, T, CT, MODE, true, 2>,
+            SPS_CUDA(cudaFuncSetAttribute(k_point<P, T, CT, MODE, 1, 2>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)POINT_SMEM_MAX));
             attr_pre2 = true;
           }
-          k_point<P, T, CT, MODE, true, 2><<<L.nitems, POINT_THREADS, smem_pre, st>>>(
+          k_point<P, T, CT, MODE, 1, 2><<<L.nitems, POINT_THREADS, smem_pre, st>>>(
               L.items, L.run_begin, L.run_cell, L.run_order, xs, pl->n, pl->y_sorted, v, u, L.geom, L.pre);
           SPS_CHECK_LAUNCH("point operator");
           if (timed) SPS_CUDA(record_event(g_prof.ev[2 * g_prof.used++ + 1], st));
           return SPS_OK;
         }
       }
-      k_point<P, T, CT, MODE, true><<<L.nitems, POINT_THREADS, smem_pre, st>>>(
+      k_point<P, T, CT, MODE, 1><<<L.nitems, POINT_THREADS, smem_pre, st>>>(
           L.items, L.run_begin, L.run_cell, L.run_order, xs, pl->n, pl->y_sorted, v, u, L.geom, L.pre);
       SPS_CHECK_LAUNCH("point operator");
       if (timed) SPS_CUDA(record_event(g_prof.ev[2 * g_prof.used++ + 1], st));
@@ -517,6 +558,34 @@ __global__ void k_basis_pre(const int* __restrict__ run_begin, const unsigned lo
   }
 }
 
+// P = 3: the 4 pieces of dimension 1 and the 16 products of the pieces of
+// dimensions 2 and 3 of every point (one thread per run), [point][20].
+template <typename CT>
+__global__ void k_basis_pre2(const int* __restrict__ run_begin, const unsigned long long* __restrict__ run_cell,
+                             int nruns, const CT* __restrict__ xs, long long n, LevelGeom geom,
+                             double* __restrict__ pre2) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nruns; r += gridDim.x * blockDim.x) {
+    const unsigned long long pc = run_cell[r];
+    double tsh[3], inv[3];
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+      const int c = (int)((pc >> (12 * p)) & 0xFFFull);
+      inv[p] = geom.inv_h[p];
+      tsh[p] = geom.lo[p] * geom.inv_h[p] + (double)c;
+    }
+    for (int i = run_begin[r]; i < run_begin[r + 1]; ++i) {
+      double b[3][4];
+#pragma unroll
+      for (int p = 0; p < 3; ++p) cubic_basis(fma((double)xs[(long long)p * n + i], inv[p], -tsh[p]), b[p]);
+      double* o = pre2 + (long long)i * PRE2_STRIDE;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) o[m] = b[0][m];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) o[4 + k] = b[1][k >> 2] * b[2][k & 3];
+    }
+  }
+}
+
 template <int P>
 int basis_pre_launch(sps_plan* pl, const Level& L, cudaStream_t st) {
   const int blocks = grid_blocks(L.nruns, 128);
@@ -527,6 +596,17 @@ int basis_pre_launch(sps_plan* pl, const Level& L, cudaStream_t st) {
     k_basis_pre<P, float><<<blocks, 128, 0, st>>>(L.run_begin, L.run_cell, L.nruns, pl->x32_sorted, pl->n,
                                                   L.geom, L.pre);
   SPS_CHECK_LAUNCH("basis precompute");
+  if constexpr (P == 3) {
+    if (L.pre2) {
+      if (pl->dtype == SPS_F64)
+        k_basis_pre2<double><<<blocks, 128, 0, st>>>(L.run_begin, L.run_cell, L.nruns, (const double*)pl->x_sorted,
+                                                     pl->n, L.geom, L.pre2);
+      else
+        k_basis_pre2<float><<<blocks, 128, 0, st>>>(L.run_begin, L.run_cell, L.nruns, pl->x32_sorted, pl->n,
+                                                    L.geom, L.pre2);
+      SPS_CHECK_LAUNCH("basis product precompute");
+    }
+  }
   return SPS_OK;
 }
 

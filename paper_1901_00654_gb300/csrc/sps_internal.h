@@ -78,6 +78,10 @@ struct Level {
   // FP64 matrix-free levels: basis values of every point, [point][dim][m]
   double* pre = nullptr;
   long long pre_cap = 0;
+  // P = 3 FP64 matrix-free levels, four-lane layout: per point the 4 pieces of
+  // dimension 1 and the 16 products of dimensions 2 and 3, [point][20]
+  double* pre2 = nullptr;
+  long long pre2_cap = 0;
   // FP32 apply of the point operator: dimensions held in a lane's registers
   // (2: 4^(P-2) lanes per run; 3: 4^(P-3) lanes per run; 0: the default for P)
   int lanes_r = 0;
@@ -183,6 +187,7 @@ constexpr size_t POINT_SMEM_MAX = 160 * 1024;   // opt-in dynamic shared memory 
 template <typename T>
 int point_op(sps_plan* pl, int g, int mode, const T* v, T* u, cudaStream_t st);
 int basis_precompute(sps_plan* pl, int g, cudaStream_t st);
+constexpr int PRE2_STRIDE = 20;   // doubles per point of Level::pre2
 int profile_begin();
 int profile_end(double* ms, unsigned long long* launches);
 bool profile_active();
