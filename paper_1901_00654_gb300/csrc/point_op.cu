@@ -99,6 +99,10 @@ k_point(const WorkItem* __restrict__ items, const int* __restrict__ run_begin,
     s_cell[e] = cl;
   }
   if (!PRE) {
+    // the host sizes the shared memory by the largest item; never stage past it
+    unsigned dsm;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dsm));
+    if (xoff + (size_t)P * npts * sizeof(CT) > dsm) return;
 #pragma unroll
     for (int p = 0; p < P; ++p)
       for (int e = threadIdx.x; e < npts; e += blockDim.x) xsh[p * npts + e] = xs[(long long)p * n + pbeg + e];
@@ -404,8 +408,8 @@ constexpr int PROFILE_MAX = 8192;
 template <int P, typename T, typename CT, int MODE>
 int launch_point(sps_plan* pl, const Level& L, const T* v, T* u, cudaStream_t st) {
   if (L.nitems == 0) return SPS_OK;
-  // patch accumulator (+ patch of v) + staged coordinates of at most runs_per_item * RUN_MAX points
-  const size_t pts = (size_t)runs_per_item(pl->P) * RUN_MAX;
+  // patch accumulator (+ patch of v) + staged coordinates of the largest item's points
+  const size_t pts = (size_t)L.max_item_pts;
   const size_t smem = (size_t)(MODE == PT_APPLY ? 2 : 1) * L.geom.patch * sizeof(T) + pts * P * sizeof(CT) + 16;
   if (smem > POINT_SMEM_MAX) {
     set_error("tile too large for the point operator's shared memory");

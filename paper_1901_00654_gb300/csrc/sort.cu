@@ -467,10 +467,12 @@ int build_level_work(sps_plan* pl, int g, cudaStream_t st) {
     k_sort_item_runs<<<nitems, 128, 0, st>>>(L.items, L.run_begin, L.run_order);
     SPS_CHECK_LAUNCH("sort item runs");
   }
-  if (nitems > 1) {
-    // Items in decreasing order of their point counts: CTAs start roughly in
-    // block order, so the large items run in the first wave and the small
-    // ones fill the tail (longest-processing-time-first scheduling).
+  L.max_item_pts = 0;
+  if (nitems > 0) {
+    // Point counts of the items: the largest sizes the point operator's shared
+    // memory.  Then the items in decreasing order of their point counts: CTAs
+    // start roughly in block order, so the large items run in the first wave
+    // and the small ones fill the tail (longest-processing-time-first).
     const long long item_words = (long long)((sizeof(WorkItem) + 3) / 4) * nitems;
     if ((e = ensure_seg(pl, 2LL * nitems + item_words))) return e;
     unsigned int* npts = (unsigned int*)pl->seg_tmp;
@@ -481,7 +483,10 @@ int build_level_work(sps_plan* pl, int g, cudaStream_t st) {
     std::vector<unsigned int> h(nitems), order(nitems);
     SPS_CUDA(cudaMemcpyAsync(h.data(), npts, sizeof(unsigned int) * nitems, cudaMemcpyDeviceToHost, st));
     SPS_CUDA(cudaStreamSynchronize(st));
-    for (unsigned int k = 0; k < nitems; ++k) order[k] = k;
+    for (unsigned int k = 0; k < nitems; ++k) {
+      order[k] = k;
+      L.max_item_pts = std::max(L.max_item_pts, (int)h[k]);
+    }
     std::stable_sort(order.begin(), order.end(), [&](unsigned a, unsigned b) { return h[a] > h[b]; });
     SPS_CUDA(cudaMemcpyAsync(perm, order.data(), sizeof(unsigned int) * nitems, cudaMemcpyHostToDevice, st));
     k_permute_items<<<grid_blocks(nitems, 256), 256, 0, st>>>(L.items, perm, (int)nitems, tmp);

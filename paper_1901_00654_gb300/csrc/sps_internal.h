@@ -20,9 +20,10 @@ constexpr int POINT_THREADS = 128;   // threads per CTA of the point operator
 
 // Lanes that share one run: 4^(P-3) for P > 3, else 1.
 inline int lanes_per_run(int P) { return P <= 3 ? 1 : (P == 4 ? 4 : 16); }
-// Runs per work item: one per thread group (two for P > 3), so an item holds at
-// most POINT_THREADS * RUN_MAX points (2048) and its coordinates fit in shared memory.
-inline int runs_per_item(int P) { return (POINT_THREADS / lanes_per_run(P)) * (P <= 3 ? 1 : 2); }
+// Runs per work item: 128 for P <= 4 (one tile of 4^4 cells in one item), 32 for
+// P = 5.  The point operator's shared memory is sized by the largest item's
+// actual point count (Level::max_item_pts), at most 128 * RUN_MAX = 2048.
+inline int runs_per_item(int P) { return P <= 4 ? 128 : 32; }
 constexpr int COARSE_MAX = 4096;     // K_1 limit of the dense coarse inverse
 
 // Geometry of one grid level, passed by value to kernels.
@@ -85,6 +86,7 @@ struct Level {
   // FP32 apply of the point operator: dimensions held in a lane's registers
   // (2: 4^(P-2) lanes per run; 3: 4^(P-3) lanes per run; 0: the default for P)
   int lanes_r = 0;
+  int max_item_pts = 0;   // points of the largest work item (sizes the staged coordinates)
   LevelVecs<double> d;
   LevelVecs<float> f;
 };
