@@ -12,14 +12,16 @@
 //    contiguous "run" (at most RUN_MAX points).  A CTA owns the runs of one
 //    tile of ts^P cells; the (ts+q)^P coefficients its points can touch are
 //    staged in shared memory.
-//  * The item's point coordinates are contiguous after the sort and are
-//    staged in shared memory with coalesced loads before the run loop.
-//  * A group of TPP = 4^(P-3) lanes (1 lane for P <= 3) takes one run at a
-//    time.  Each lane owns 64 (or 4^P) of the cell's (q+1)^P coefficients and
-//    keeps their partial sums in registers while it walks the run, so the
-//    scatter costs one shared-memory atomic per coefficient per run instead
-//    of one per point.  The gather is sum-factorised over the lane's last
-//    three dimensions and reduced across the group with shuffles.
+//  * The item's point coordinates and run table are contiguous after the
+//    sort and are staged in shared memory with coalesced loads before the run
+//    loop (FP64 levels read precomputed basis values instead of coordinates).
+//  * A group of TPP = 4^(P-R) lanes takes one run at a time, R = 2 or 3 being
+//    the number of trailing dimensions a lane holds: each lane owns 4^R of the
+//    cell's (q+1)^P coefficients (16 or 64) and keeps their partial sums in
+//    registers while it walks the run, so the scatter costs one shared-memory
+//    atomic per coefficient per run instead of one per point.  The gather is
+//    sum-factorised over the lane's R dimensions and reduced across the group
+//    with shuffles.  The layout per level is chosen by the autotuner.
 //  * The shared accumulator is flushed to global memory with atomics, since
 //    neighbouring tiles overlap in q layers of coefficients.
 #include <cuda_runtime.h>
@@ -154,7 +156,20 @@ k_point(const WorkItem* __restrict__ items, const int* __restrict__ run_begin,
   // (1-t)^3/6, (3t^3-6t^2+4)/6, (-3t^3+3t^2+3t+1)/6 and t^3/6.  Used by the
   // register-light layouts (RR > 0); elsewhere the 4F extra registers would
   // cost occupancy, and the lane evaluates all four pieces and selects.
-  constexpr bool ONEPIECE = RR > 0 && F > 0;
+  // P = 4, FP32, 16 lanes per run: the 16 (dimension, piece) values of a
+  // point are computed once each -- lane l evaluates piece l & 3 of dimension
+  // l >> 2 -- and shared with shuffles, instead of every lane evaluating the
+  // pieces of all four dimensions.
+  constexpr bool SHARED_BASIS = P == 4 && R == 2 && !PRE && sizeof(T) == 4 && MODE == PT_APPLY;
+  const int sdim = SHARED_BASIS ? (glane >> 2) : 0;
+  const int spc = glane & 3;
+  const T sinv = sdim == 0 ? inv[0] : sdim == 1 ? inv[P > 1 ? 1 : 0] : sdim == 2 ? inv[P > 2 ? 2 : 0]
+                                                                                 : inv[P > 3 ? 3 : 0];
+  const T sc0 = spc == 0 ? T(1.0 / 6.0) : spc == 1 ? T(2.0 / 3.0) : spc == 2 ? T(1.0 / 6.0) : T(0);
+  const T sc1 = spc == 0 ? T(-0.5) : spc == 1 ? T(0) : spc == 2 ? T(0.5) : T(0);
+  const T sc2 = spc == 0 ? T(0.5) : spc == 1 ? T(-1) : spc == 2 ? T(0.5) : T(0);
+  const T sc3 = spc == 0 ? T(-1.0 / 6.0) : spc == 1 ? T(0.5) : spc == 2 ? T(-0.5) : T(1.0 / 6.0);
+  constexpr bool ONEPIECE = RR > 0 && F > 0 && !SHARED_BASIS;
   constexpr int NF = ONEPIECE ? F : 1;
   T pc0[NF], pc1[NF], pc2[NF], pc3[NF];
 #pragma unroll
@@ -181,6 +196,8 @@ k_point(const WorkItem* __restrict__ items, const int* __restrict__ run_begin,
       base += o * geom.Es[p];
       tsh[p] = loinv[p] + T(c);   // t = x * inv - (lo * inv + c)
     }
+    const T stsh = sdim == 0 ? tsh[0] : sdim == 1 ? tsh[P > 1 ? 1 : 0] : sdim == 2 ? tsh[P > 2 ? 2 : 0]
+                                                                                : tsh[P > 3 ? 3 : 0];
     const int e0 = R >= 3 ? geom.Es[P - 3] : 0;
     const int e1 = R >= 2 ? geom.Es[P - 2] : 0;
     auto vidx = [&](int k) -> int {
@@ -237,6 +254,15 @@ k_point(const WorkItem* __restrict__ items, const int* __restrict__ run_begin,
         for (int p = 0; p < F; ++p) {   // select without dynamic register indexing
           const int m = mfix[p];
           fixw *= m == 0 ? bv[p][0] : m == 1 ? bv[p][1] : m == 2 ? bv[p][2] : bv[p][3];
+        }
+      } else if (SHARED_BASIS) {
+        const T t = fma(T(xsh[sdim * npts + (i - pbeg)]), sinv, -stsh);
+        const T val = fma(fma(fma(sc3, t, sc2), t, sc1), t, sc0);
+        fixw = __shfl_sync(gmask, val, mfix[0], TPP) * __shfl_sync(gmask, val, 4 + mfix[F > 1 ? 1 : 0], TPP);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          bv[P - 2][m] = __shfl_sync(gmask, val, 8 + m, TPP);
+          bv[P - 1][m] = __shfl_sync(gmask, val, 12 + m, TPP);
         }
       } else {
 #pragma unroll
