@@ -534,10 +534,11 @@ __device__ void cta_solve(const BatchProblem& pb, BatchOut* out, double* sh, Tea
 // of the nbig largest problems from queue[0] and solves it with all C CTAs.
 // Phase 2: every CTA takes the next remaining problem from queue[1] and
 // solves it alone.  Problems arrive in decreasing cost order.
-template <int C>
+// C is the cluster size of the launch (1: no cluster); one instantiation
+// serves every C, since the team's size is a run-time value anyway.
 __global__ void __launch_bounds__(BT, 1) k_batch_solve(const BatchProblem* __restrict__ probs,
                                                        const int* __restrict__ order, int count, int nbig,
-                                                       int* queue, BatchOut* __restrict__ outs) {
+                                                       int* queue, BatchOut* __restrict__ outs, int C) {
   __shared__ double sh[BT / 32];
   __shared__ int cur;
   Team tm;
@@ -674,9 +675,7 @@ int solve_batch(sps_plan* const* plans, int count, double* const* coefs, int mem
     oc.attrs = &oa;
     oc.numAttrs = 1;
     int clusters = 0;
-    cudaError_t oe = C == 2 ? cudaOccupancyMaxActiveClusters(&clusters, k_batch_solve<2>, &oc)
-                     : C == 4 ? cudaOccupancyMaxActiveClusters(&clusters, k_batch_solve<4>, &oc)
-                              : cudaOccupancyMaxActiveClusters(&clusters, k_batch_solve<8>, &oc);
+    cudaError_t oe = cudaOccupancyMaxActiveClusters(&clusters, k_batch_solve, &oc);
     if (oe != cudaSuccess || clusters < 1) {
       cudaGetLastError();
       C = 1;
@@ -715,13 +714,7 @@ int solve_batch(sps_plan* const* plans, int count, double* const* coefs, int mem
     const int* a1 = (const int*)(dev + off_o);
     int* a3 = (int*)(dev + off_q);
     BatchOut* a4 = (BatchOut*)(dev + off_r);
-    cudaError_t le;
-    switch (C) {
-      case 1: le = cudaLaunchKernelEx(&cfg, k_batch_solve<1>, a0, a1, count, nbig, a3, a4); break;
-      case 2: le = cudaLaunchKernelEx(&cfg, k_batch_solve<2>, a0, a1, count, nbig, a3, a4); break;
-      case 4: le = cudaLaunchKernelEx(&cfg, k_batch_solve<4>, a0, a1, count, nbig, a3, a4); break;
-      default: le = cudaLaunchKernelEx(&cfg, k_batch_solve<8>, a0, a1, count, nbig, a3, a4); break;
-    }
+    const cudaError_t le = cudaLaunchKernelEx(&cfg, k_batch_solve, a0, a1, count, nbig, a3, a4, C);
     if (le != cudaSuccess) {
       cudaGraph_t dummy;
       cudaStreamEndCapture(cs, &dummy);
