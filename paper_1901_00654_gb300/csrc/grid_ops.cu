@@ -33,7 +33,7 @@ __global__ void k_pen_sweep(int stage, long long K, long long strd, int Jp, cons
     const T* M = band + (long long)j * BAND;
     const T* D1 = band + ((long long)Jp + j) * BAND;
     const T* D2 = band + (2LL * Jp + j) * BAND;
-    T a0 = T(0), a1 = T(0), a2 = T(0);
+    T a0 = T(0), a1 = T(0), a2 = T(0), h = T(0);   // h = D1 x1: a2 gets 2h after the taps
 #pragma unroll
     for (int o = -Q; o <= Q; ++o) {
       const int jj = j + o;
@@ -53,9 +53,11 @@ __global__ void k_pen_sweep(int stage, long long K, long long strd, int Jp, cons
           a0 = fma(m, x0, a0);
           a1 = fma(m, x1, fma(d1, x0, a1));
         }
-        a2 = fma(m, x2, fma(T(2) * d1, x1, fma(d2, x0, a2)));
+        a2 = fma(m, x2, fma(d2, x0, a2));
+        h = fma(d1, x1, h);
       }
     }
+    if (stage == 1 || stage == 2) a2 = fma(T(2), h, a2);
     if (stage <= 1) {
       o0[k] = a0;
       o1[k] = a1;
