@@ -315,9 +315,8 @@ __global__ void k_d2f_scaled(const double* __restrict__ a, float* __restrict__ b
 // the leading P-1 offsets and walks the last offset as a straight loop; the
 // SPMV_Y partial sums of a row are added in shared memory.  Offsets outside the
 // grid are skipped by range, not by division.
-constexpr int SPMV_Y = 8;
 
-template <int P, typename T>
+template <int P, typename T, int SPMV_Y>
 __global__ void __launch_bounds__(32 * SPMV_Y) k_stencil_spmv(const T* __restrict__ A, LevelGeom geom,
                                                               const T* __restrict__ v, T* __restrict__ u) {
   __shared__ T part[SPMV_Y][33];
@@ -763,13 +762,26 @@ int stencil_apply(sps_plan* pl, int g, const T* v, T* u, cudaStream_t st) {
   const T* A = nullptr;
   if constexpr (sizeof(T) == 8) A = (const T*)L.st_d; else A = (const T*)L.st_f;
   const int blocks = (int)((L.geom.K + 31) / 32);
-  const dim3 tb(32, SPMV_Y);
-  switch (pl->P) {
-    case 1: k_stencil_spmv<1, T><<<blocks, tb, 0, st>>>(A, L.geom, v, u); break;
-    case 2: k_stencil_spmv<2, T><<<blocks, tb, 0, st>>>(A, L.geom, v, u); break;
-    case 3: k_stencil_spmv<3, T><<<blocks, tb, 0, st>>>(A, L.geom, v, u); break;
-    case 4: k_stencil_spmv<4, T><<<blocks, tb, 0, st>>>(A, L.geom, v, u); break;
-    default: k_stencil_spmv<5, T><<<blocks, tb, 0, st>>>(A, L.geom, v, u); break;
+  // 8 offset groups per row; 32 on small levels, where a few dozen CTAs
+  // cannot fill the GPU and each thread's chain of offsets sets the time
+  if (L.geom.K <= 16384) {
+    const dim3 tb(32, 32);
+    switch (pl->P) {
+      case 1: k_stencil_spmv<1, T, 32><<<blocks, tb, 0, st>>>(A, L.geom, v, u); break;
+      case 2: k_stencil_spmv<2, T, 32><<<blocks, tb, 0, st>>>(A, L.geom, v, u); break;
+      case 3: k_stencil_spmv<3, T, 32><<<blocks, tb, 0, st>>>(A, L.geom, v, u); break;
+      case 4: k_stencil_spmv<4, T, 32><<<blocks, tb, 0, st>>>(A, L.geom, v, u); break;
+      default: k_stencil_spmv<5, T, 32><<<blocks, tb, 0, st>>>(A, L.geom, v, u); break;
+    }
+  } else {
+    const dim3 tb(32, 8);
+    switch (pl->P) {
+      case 1: k_stencil_spmv<1, T, 8><<<blocks, tb, 0, st>>>(A, L.geom, v, u); break;
+      case 2: k_stencil_spmv<2, T, 8><<<blocks, tb, 0, st>>>(A, L.geom, v, u); break;
+      case 3: k_stencil_spmv<3, T, 8><<<blocks, tb, 0, st>>>(A, L.geom, v, u); break;
+      case 4: k_stencil_spmv<4, T, 8><<<blocks, tb, 0, st>>>(A, L.geom, v, u); break;
+      default: k_stencil_spmv<5, T, 8><<<blocks, tb, 0, st>>>(A, L.geom, v, u); break;
+    }
   }
   SPS_CHECK_LAUNCH("stencil apply");
   return SPS_OK;
