@@ -23,13 +23,14 @@ constexpr int RED_BLOCKS = 304;      // 2 per SM; fixed so reductions are determ
 //   W0' = M W0,  W1' = M W1 + D1 W0,  W2' = M W2 + 2 D1 W1 + D2 W0,
 // with M = Psi^p_0, D1 = Psi^p_1, D2 = Psi^p_2 banded (2q+1 diagonals).
 // stage: 0 first dimension, 1 middle, 2 last, 3 only dimension.
-template <typename T>
-__global__ void k_pen_sweep(int stage, long long K, long long strd, int Jp, const T* __restrict__ band,
+// IT: index type -- 32-bit unsigned when every index fits (one integer
+// division instead of a 64-bit division routine per element), else 64-bit.
+template <typename T, typename IT>
+__global__ void k_pen_sweep(int stage, IT K, IT strd, int Jp, const T* __restrict__ band,
                             const T* __restrict__ w0, const T* __restrict__ w1, const T* __restrict__ w2,
                             T* __restrict__ o0, T* __restrict__ o1, T* __restrict__ o2, T scale) {
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < K;
-       k += (long long)gridDim.x * blockDim.x) {
-    const int j = (int)((k / strd) % Jp);
+  for (IT k = (IT)blockIdx.x * blockDim.x + threadIdx.x; k < K; k += (IT)gridDim.x * blockDim.x) {
+    const int j = (int)((k / strd) % (IT)Jp);
     const T* M = band + (long long)j * BAND;
     const T* D1 = band + ((long long)Jp + j) * BAND;
     const T* D2 = band + (2LL * Jp + j) * BAND;
@@ -38,7 +39,7 @@ __global__ void k_pen_sweep(int stage, long long K, long long strd, int Jp, cons
     for (int o = -Q; o <= Q; ++o) {
       const int jj = j + o;
       if (jj < 0 || jj >= Jp) continue;
-      const long long kk = k + (long long)o * strd;
+      const IT kk = k + (IT)((long long)o * (long long)strd);
       const T m = M[o + Q], d1 = D1[o + Q], d2 = D2[o + Q];
       if (stage == 0) {
         const T x = w0[kk];
@@ -95,15 +96,15 @@ __global__ void k_pen_diag(long long K, LevelGeom geom, const double* __restrict
 __constant__ double c_subdiv[Q + 2] = {1.0 / 8, 4.0 / 8, 6.0 / 8, 4.0 / 8, 1.0 / 8};
 
 // out (fine along the swept mode) = I_1d * in (coarse along it).
-template <typename T>
-__global__ void k_prolong_sweep(long long Kout, long long inner, int Jin, int Jout, const T* __restrict__ in,
+template <typename T, typename IT>
+__global__ void k_prolong_sweep(IT Kout, IT inner, int Jin, int Jout, const T* __restrict__ in,
                                 T* __restrict__ out, int subtract) {
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < Kout;
-       k += (long long)gridDim.x * blockDim.x) {
-    const long long outer = k / ((long long)Jout * inner);
-    const long long rem = k - outer * Jout * inner;
+  const IT blk = (IT)Jout * inner;
+  for (IT k = (IT)blockIdx.x * blockDim.x + threadIdx.x; k < Kout; k += (IT)gridDim.x * blockDim.x) {
+    const IT outer = k / blk;
+    const IT rem = k - outer * blk;
     const int i = (int)(rem / inner);
-    const long long ii = rem - (long long)i * inner;
+    const IT ii = rem - (IT)i * inner;
     T s = T(0);
 #pragma unroll
     for (int kk = 0; kk <= Q + 1; ++kk) {
@@ -111,28 +112,28 @@ __global__ void k_prolong_sweep(long long Kout, long long inner, int Jin, int Jo
       if (num & 1) continue;
       const int j = num >> 1;
       if (j < 0 || j >= Jin) continue;
-      s = fma(T(c_subdiv[kk]), in[(outer * Jin + j) * inner + ii], s);
+      s = fma(T(c_subdiv[kk]), in[(outer * (IT)Jin + (IT)j) * inner + ii], s);
     }
     if (subtract) out[k] -= s; else out[k] = s;
   }
 }
 
 // out (coarse along the mode) = I_1d' * (in - inb) (fine along it).
-template <typename T>
-__global__ void k_restrict_sweep(long long Kout, long long inner, int Jin, int Jout, const T* __restrict__ in,
+template <typename T, typename IT>
+__global__ void k_restrict_sweep(IT Kout, IT inner, int Jin, int Jout, const T* __restrict__ in,
                                  const T* __restrict__ inb, T* __restrict__ out) {
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < Kout;
-       k += (long long)gridDim.x * blockDim.x) {
-    const long long outer = k / ((long long)Jout * inner);
-    const long long rem = k - outer * Jout * inner;
+  const IT blk = (IT)Jout * inner;
+  for (IT k = (IT)blockIdx.x * blockDim.x + threadIdx.x; k < Kout; k += (IT)gridDim.x * blockDim.x) {
+    const IT outer = k / blk;
+    const IT rem = k - outer * blk;
     const int j = (int)(rem / inner);
-    const long long ii = rem - (long long)j * inner;
+    const IT ii = rem - (IT)j * inner;
     T s = T(0);
 #pragma unroll
     for (int kk = 0; kk <= Q + 1; ++kk) {
       const int i = 2 * j - Q + kk;
       if (i < 0 || i >= Jin) continue;
-      const long long src = (outer * Jin + i) * inner + ii;
+      const IT src = (outer * (IT)Jin + (IT)i) * inner + ii;
       const T val = inb ? in[src] - inb[src] : in[src];
       s = fma(T(c_subdiv[kk]), val, s);
     }
@@ -581,9 +582,18 @@ int penalty_apply(sps_plan* pl, int g, const T* v, T* out, double scale, cudaStr
   const int P = pl->P;
   const T* band = vecs<T>(L).band;
   const int blocks = grid_blocks(G.K, EW_THREADS);
+  const bool i32 = G.K < (1LL << 31);
+  auto sweep = [&](int stage, int p, const T* bp, const T* w0, const T* w1, const T* w2, T* o0, T* o1, T* o2,
+                   T sc) {
+    if (i32)
+      k_pen_sweep<T, unsigned><<<blocks, EW_THREADS, 0, st>>>(stage, (unsigned)G.K, (unsigned)G.stride[p], G.J[p],
+                                                              bp, w0, w1, w2, o0, o1, o2, sc);
+    else
+      k_pen_sweep<T, long long><<<blocks, EW_THREADS, 0, st>>>(stage, G.K, G.stride[p], G.J[p], bp, w0, w1, w2, o0,
+                                                               o1, o2, sc);
+  };
   if (P == 1) {
-    k_pen_sweep<T><<<blocks, EW_THREADS, 0, st>>>(3, G.K, G.stride[0], G.J[0], band, v, nullptr, nullptr, nullptr,
-                                                   nullptr, out, T(scale));
+    sweep(3, 0, band, v, nullptr, nullptr, nullptr, nullptr, out, T(scale));
     SPS_CHECK_LAUNCH("penalty");
     return SPS_OK;
   }
@@ -593,15 +603,12 @@ int penalty_apply(sps_plan* pl, int g, const T* v, T* out, double scale, cudaStr
   for (int p = 0; p < P; ++p) {
     const T* bp = band + boff;
     if (p == 0) {
-      k_pen_sweep<T><<<blocks, EW_THREADS, 0, st>>>(0, G.K, G.stride[p], G.J[p], bp, v, nullptr, nullptr, A[0], A[1],
-                                                     A[2], T(1));
+      sweep(0, p, bp, v, nullptr, nullptr, A[0], A[1], A[2], T(1));
     } else if (p < P - 1) {
-      k_pen_sweep<T><<<blocks, EW_THREADS, 0, st>>>(1, G.K, G.stride[p], G.J[p], bp, A[0], A[1], A[2], B[0], B[1],
-                                                     B[2], T(1));
+      sweep(1, p, bp, A[0], A[1], A[2], B[0], B[1], B[2], T(1));
       std::swap(A, B);
     } else {
-      k_pen_sweep<T><<<blocks, EW_THREADS, 0, st>>>(2, G.K, G.stride[p], G.J[p], bp, A[0], A[1], A[2], nullptr,
-                                                     nullptr, out, T(scale));
+      sweep(2, p, bp, A[0], A[1], A[2], nullptr, nullptr, out, T(scale));
     }
     SPS_CHECK_LAUNCH("penalty sweep");
     boff += 3LL * G.J[p] * BAND;
@@ -633,8 +640,12 @@ int prolong_sub(sps_plan* pl, int g, const T* c, T* f, int mode, cudaStream_t st
     const long long Kout = outer * Gf.J[p] * inner;
     const bool last = p == P - 1;
     T* out = last ? f : tmp[p & 1];
-    k_prolong_sweep<T><<<grid_blocks(Kout, EW_THREADS), EW_THREADS, 0, st>>>(Kout, inner, Gc.J[p], Gf.J[p], in, out,
-                                                                              last ? mode : 0);
+    if (Gf.K < (1LL << 31))
+      k_prolong_sweep<T, unsigned><<<grid_blocks(Kout, EW_THREADS), EW_THREADS, 0, st>>>(
+          (unsigned)Kout, (unsigned)inner, Gc.J[p], Gf.J[p], in, out, last ? mode : 0);
+    else
+      k_prolong_sweep<T, long long><<<grid_blocks(Kout, EW_THREADS), EW_THREADS, 0, st>>>(
+          Kout, inner, Gc.J[p], Gf.J[p], in, out, last ? mode : 0);
     SPS_CHECK_LAUNCH("prolong");
     in = out;
   }
@@ -658,8 +669,12 @@ int restrict_res(sps_plan* pl, int g, const T* f, const T* fb, T* c, cudaStream_
     for (int q = 0; q < p; ++q) outer *= Gc.J[q];
     const long long Kout = outer * Gc.J[p] * inner;
     T* out = p == P - 1 ? c : tmp[p & 1];
-    k_restrict_sweep<T><<<grid_blocks(Kout, EW_THREADS), EW_THREADS, 0, st>>>(Kout, inner, Gf.J[p], Gc.J[p], in, inb,
-                                                                               out);
+    if (Gf.K < (1LL << 31))
+      k_restrict_sweep<T, unsigned><<<grid_blocks(Kout, EW_THREADS), EW_THREADS, 0, st>>>(
+          (unsigned)Kout, (unsigned)inner, Gf.J[p], Gc.J[p], in, inb, out);
+    else
+      k_restrict_sweep<T, long long><<<grid_blocks(Kout, EW_THREADS), EW_THREADS, 0, st>>>(
+          Kout, inner, Gf.J[p], Gc.J[p], in, inb, out);
     SPS_CHECK_LAUNCH("restrict");
     in = out;
     inb = nullptr;
