@@ -1049,8 +1049,8 @@ int sps_solve_batch(sps_plan* const* plans, int count, double* const* coefs, int
   }
   for (int i = 0; i < count; ++i) {
     SPS_TRY(check_plan_points(plans[i]));
-    if (plans[i]->P > 3 || !coefs[i]) {
-      set_error("batched solves take P <= 3 and a coefficient buffer per problem");
+    if (plans[i]->P > 3 || !coefs[i] || plans[i]->lev[plans[i]->G - 1].geom.K >= (1LL << 31)) {
+      set_error("batched solves take P <= 3, fewer than 2^31 coefficients and a coefficient buffer per problem");
       return SPS_EINVAL;
     }
     if (plans[i]->rhs_norm == 0.0) {

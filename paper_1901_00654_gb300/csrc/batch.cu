@@ -229,7 +229,7 @@ __device__ void cta_penalty(const LevelGeom& g, const T* band, const T* v, T* ou
     T* o1 = t[3 * ping + 1];
     T* o2 = t[3 * ping + 2];
     for (long long k = tm.start(); k < K; k += tm.stride()) {
-      const int j = (int)((k / strd) % Jp);
+      const int j = (int)(((unsigned)k / (unsigned)strd) % (unsigned)Jp);   // K < 2^31 (checked by the host)
       T a0 = T(0), a1 = T(0), a2 = T(0);
       for (int o = -Q; o <= Q; ++o) {
         const int jj = j + o;
@@ -273,7 +273,7 @@ __device__ void cta_apply(const BatchProblem& pb, int lev, const T* v, T* u, T* 
     const LevelGeom& g = L.geom;
     for (long long k = tm.start(); k < g.K; k += tm.stride()) {
       int j[P];
-      for (int p = 0; p < P; ++p) j[p] = (int)((k / g.stride[p]) % g.J[p]);
+      for (int p = 0; p < P; ++p) j[p] = (int)(((unsigned)k / (unsigned)g.stride[p]) % (unsigned)g.J[p]);
       T acc = T(0);
       for (int s = 0; s < L.S; ++s) {
         int ss = s;
@@ -312,10 +312,11 @@ __device__ void cta_restrict(const BatchProblem& pb, int g, const float* f, cons
     const long long Kout = outer * Jout * inner;
     float* out = p == pb.P - 1 ? c : pb.ftmp[6 + (p & 1)];
     for (long long k = tm.start(); k < Kout; k += tm.stride()) {
-      const long long o = k / ((long long)Jout * inner);
-      const long long rem = k - o * Jout * inner;
-      const int j = (int)(rem / inner);
-      const long long ii = rem - (long long)j * inner;
+      const unsigned blk = (unsigned)Jout * (unsigned)inner, ku = (unsigned)k;
+      const long long o = ku / blk;
+      const unsigned rem = ku - (unsigned)o * blk;
+      const int j = (int)(rem / (unsigned)inner);
+      const long long ii = rem - (unsigned)j * (unsigned)inner;
       float s = 0.0f;
       for (int kk = 0; kk <= Q + 1; ++kk) {
         const int i = 2 * j - Q + kk;
@@ -347,10 +348,11 @@ __device__ void cta_prolong_sub(const BatchProblem& pb, int g, const float* c, f
     const bool last = p == pb.P - 1;
     float* out = last ? f : pb.ftmp[6 + (p & 1)];
     for (long long k = tm.start(); k < Kout; k += tm.stride()) {
-      const long long o = k / ((long long)Jout * inner);
-      const long long rem = k - o * Jout * inner;
-      const int i = (int)(rem / inner);
-      const long long ii = rem - (long long)i * inner;
+      const unsigned blk = (unsigned)Jout * (unsigned)inner, ku = (unsigned)k;
+      const long long o = ku / blk;
+      const unsigned rem = ku - (unsigned)o * blk;
+      const int i = (int)(rem / (unsigned)inner);
+      const long long ii = rem - (unsigned)i * (unsigned)inner;
       float s = 0.0f;
       for (int kk = 0; kk <= Q + 1; ++kk) {
         const int num = i + Q - kk;
