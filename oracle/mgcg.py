@@ -4,7 +4,7 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).  FP64 throughout; all
 operators are assembled sparse matrices, so every step can be checked by eye
 against the algorithms of Section 3.2.
 
-Readings (listed in DESIGN.md):
+Readings of the paper used here:
 * Step size of Algorithm 8: w = r'z / p'v (the preconditioned CG step; the
   printed |r|^2 is the unpreconditioned one and is inconsistent with the
   printed beta = r'z / r~'z~).

@@ -2,7 +2,7 @@
 
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).  FP64 throughout.
 
-Readings of the paper used here (each is listed in the design doc):
+Readings of the paper used here:
 * Knots: extended uniform ("cardinal") knots.  With N intervals of width
   h = (hi - lo)/N on [lo, hi], knot t_i = lo + (i - q) h for i = 0..N+2q, and
   basis function j = 0..N+q-1 lives on [t_j, t_{j+q+1}].  J = N + q matches
