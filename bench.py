@@ -19,6 +19,7 @@ import argparse
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -33,11 +34,6 @@ import numpy as np  # noqa: E402
 import workloads as W  # noqa: E402
 
 METRIC = "MG-PCG solves/s & operator Gpoint-applies/s at rel.res 1e-8; p50/p99 vs plain FP64"
-# ncu dram__bytes_read.sum + dram__bytes_write.sum of one FP64 apply launch on the 64^3,
-# 10^6-point workload at tile side 4, four lanes per run, precomputed basis products
-# (profiles/k_point_fp64_p3_n64_1e6pts.md)
-POINT_F64_TRAFFIC_BYTES = 166.79808e6 + 3.586304e6
-POINT_F64_TRAFFIC_SHAPE = [4, 2]
 
 
 def make_problem(name: str, n: int | None):
@@ -54,6 +50,56 @@ def workload_desc(pr) -> str:
     return "%s: P=%d q=3 N=%s (K=%d) n=%d levels=%d lambda=%g tol=%g %s" % (
         pr.name, pr.P, "x".join(str(v) for v in pr.intervals), pr.K, pr.n, pr.levels, pr.lam, pr.tol,
         "FP32 x/y, mixed precision" if pr.precision == "mixed" else "FP64")
+
+
+def _peaks() -> dict:
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+HBM_GBS = float(_peaks().get("hbm_gbs", 6800.0))   # measured copy bandwidth (fallback 6.8 TB/s)
+
+
+def point_traffic(kind: str, pr, shape) -> dict | None:
+    """DRAM bytes (read + write) of one apply launch of the point operator,
+    scaled by the number of points from the ncu capture recorded in
+    profiles/traffic.json for this kernel, workload and launch shape; None when
+    no capture matches."""
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    except (OSError, ValueError):
+        return None
+    for c in rec.get("captures", []):
+        if c["kernel"] == kind and c["workload"] == pr.name and c["P"] == pr.P and list(c["shape"]) == list(shape):
+            return {"bytes": c["dram_bytes_per_launch"] * pr.n / c["points"],
+                    "source": "%s (%s), scaled from %d to %d points" % (c["summary"], c["metric"], c["points"], pr.n)}
+    return None
+
+
+def golden_alpha(pr):
+    """The oracle's converged coefficients of this workload (tests/golden), if
+    recorded for exactly these inputs."""
+    import hashlib
+    path = os.path.join(GOLDEN_DIR, "%s_alpha.json" % pr.name)
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path))
+    sha = lambda a: hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest()
+    if rec.get("x_sha256") != sha(pr.x) or rec.get("y_sha256") != sha(pr.y):
+        return None
+    return np.load(os.path.join(GOLDEN_DIR, "%s_alpha.npy" % pr.name))
+
+
+def coef_error(coef_dev, gold) -> dict:
+    c = coef_dev.cpu().numpy()
+    return {"max_rel": float(np.max(np.abs(c - gold)) / np.max(np.abs(gold))),
+            "l2_rel": float(np.linalg.norm(c - gold) / np.linalg.norm(gold)),
+            "oracle": "tier-2 MG-PCG converged to rel.res 1e-15 (tests/golden)"}
+
+
+GOLDEN_DIR = os.path.join(ROOT, "tests", "golden")
 
 
 # ---------------------------------------------------------------- clocks
@@ -109,66 +155,121 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- reference arm (CPU oracle)
 
-def oracle_sample(pr, sweeps_per_solve: float, n_sample: int, reps: int) -> dict:
-    """Time the oracle's matrix-free apply u = Phi'(Phi v) on the first
-    n_sample points and scale to solves/s of the full workload:
-    t_solve = sweeps_per_solve * t_sample * n / n_sample.  The oracle's
-    penalty, transfer and setup work is not counted, which favours it."""
-    from oracle import sampled
-    v = np.random.default_rng(0).standard_normal(pr.K)
-    xs = pr.x[:n_sample]
-    best = math.inf
-    t_all = 0.0
-    for _ in range(reps):
+def host_cpu() -> dict:
+    """CPU model and core count of this host (recorded beside every oracle timing)."""
+    model = platform.processor() or platform.machine()
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Vendor ID") and ":" in line:
+                model = line.split(":", 1)[1].strip()
+                if line.startswith("Model name"):
+                    break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"cpu_model": model, "host_cores": os.cpu_count(), "machine": platform.machine()}
+
+
+
+
+def oracle_iterations(pr) -> tuple:
+    """Outer iterations the oracle's own MG-PCG took to rel.res 1e-8 on this
+    workload, measured by running it to convergence (tests/golden/*.json,
+    written by tests/golden/make_scale_alpha.py), or (None, why)."""
+    path = os.path.join(GOLDEN_DIR, "%s_alpha.json" % pr.name)
+    if not os.path.exists(path):
+        return None, "no recorded oracle solve for workload %s" % pr.name
+    rec = json.load(open(path))
+    return int(rec["iterations_to_1e-8"]), path
+
+
+class OracleSolveTiming:
+    """The oracle's solve of a workload, timed on this host's cores.
+
+    PR1-sized problems (K <= 5e4): the tier-1 direct solve (assembly + banded
+    Cholesky), timed whole.  The scale workload: the tier-2 MG-PCG (Algorithm 8
+    on assembled matrices, Galerkin coarse operators).  Its set-up is timed once
+    on the first n_sample points, the part proportional to n (assembly of Phi
+    and Phi'Phi) scaled to all n; each `step` then times real MG-PCG iterations
+    at the full K (their cost depends on K and the stencil, not on n), and a
+    solve is priced as set-up + (the oracle's own iteration count to 1e-8) x
+    (seconds per iteration)."""
+
+    def __init__(self, pr, n_sample: int):
+        from oracle import mgcg, spline
+        self.pr = pr
+        self.kind = "direct" if pr.K <= 50_000 else "tier2"
+        self.info = host_cpu()
+        self.iters = None
+        if self.kind == "direct":
+            return
+        self.iters, self.iters_src = oracle_iterations(pr)
+        ns = min(pr.n, n_sample)
+        xs, ys = pr.x[:ns], pr.y[:ns]
         t0 = time.perf_counter()
-        sampled.apply_phitphi_chunked(xs, v, pr.lo, pr.hi, pr.intervals, pr.q)
+        spline.system(xs, ys, pr.lo, pr.hi, pr.intervals, pr.q, pr.lam)
+        t_sys = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        self.H = mgcg.build_hierarchy(xs, ys, pr.lo, pr.hi, pr.intervals, pr.q, pr.lam, pr.levels, omega=0.5,
+                                      galerkin=True)
+        t_build = time.perf_counter() - t0
+        self.setup_s = t_build + t_sys * (pr.n / ns - 1.0)
+        self.sample = ns
+        self.t_sys, self.t_build = t_sys, t_build
+
+    def step(self, iters: int = 1) -> float:
+        """Time one bounded sample; returns its seconds."""
+        from oracle import mgcg, spline
+        pr = self.pr
+        t0 = time.perf_counter()
+        if self.kind == "direct":
+            A, b, _, _ = spline.system(pr.x, pr.y, pr.lo, pr.hi, pr.intervals, pr.q, pr.lam)
+            mgcg.solve_direct(A, b)
+            self.solve_s = time.perf_counter() - t0
+            return self.solve_s
+        mgcg.mgcg(self.H, 0.0, max_iter=iters)     # `iters` iterations (tol 0 never stops early)
         dt = time.perf_counter() - t0
-        t_all += dt
-        best = min(best, dt)
-    t_sweep = best * pr.n / n_sample
-    t_solve = sweeps_per_solve * t_sweep
-    return {"value": 1.0 / t_solve, "unit": "solves/s", "cores": 1, "kind": "oracle",
-            "sample": ("oracle Phi'(Phi v) on %d of %d points, best of %d (%.1f s CPU), scaled by n and by "
-                       "%.0f point sweeps per solve; penalty/transfer/setup not counted" %
-                       (n_sample, pr.n, reps, t_all, sweeps_per_solve)),
-            "sweep_s_full": t_sweep}
+        self.iter_s = dt / iters
+        return dt
 
+    def solve_seconds(self) -> float:
+        if self.kind == "direct":
+            return self.solve_s
+        return self.setup_s + self.iters * self.iter_s
 
-def sweeps_per_solve(iters: int, levels: int, nu1: int = 1, nu2: int = 1) -> float:
-    # outer apply + per V-cycle (nu1 + nu2 + 1) sweeps on every level above the coarsest,
-    # one V-cycle before the loop and one per iteration
-    return iters + (iters + 1) * (nu1 + nu2 + 1) * (levels - 1)
-
-
-# MG-PCG iterations of the workloads to their tolerances (omega = 4/(3 lambda_max),
-# nu1 = nu2 = 1): the reference arm prices the oracle's solve at this many outer
-# iterations.  The library and the oracle take the same iteration counts at equal
-# damping (pinned by the parity tests on smaller problems).
-REF_ITERS = {"scale": 686, "mixed": 5484, "pr1": 39}
+    def describe(self) -> str:
+        if self.kind == "direct":
+            return ("oracle tier-1 direct solve (sparse assembly + LAPACK banded Cholesky) of the whole workload, "
+                    "timed whole; single-threaded assembly, LAPACK threads as the host's BLAS sets")
+        return ("oracle tier-2 MG-PCG (assembled matrices, Galerkin coarse operators): set-up %.1f s (hierarchy on "
+                "%d of %d points %.1f s, Phi/Phi'Phi assembly %.1f s scaled to all points) + %d iterations "
+                "(the oracle's own count to rel.res 1e-8, from %s) x %.3f s per iteration timed at the full K; "
+                "single-threaded sparse products" % (self.setup_s, self.sample, self.pr.n, self.t_build, self.t_sys,
+                                                     self.iters, os.path.relpath(self.iters_src, ROOT), self.iter_s))
 
 
 def run_reference(args, pr):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    iters = args.ref_iters if args.ref_iters else REF_ITERS.get(pr.name, 12)
-    sw = sweeps_per_solve(iters, pr.levels)
-    n_sample = min(pr.n, args.ref_sample)
+    if pr.K > 50_000 and oracle_iterations(pr)[0] is None:
+        print(json.dumps({"impl": "reference", "unavailable": oracle_iterations(pr)[1]}), flush=True)
+        return
+    t_wall = time.perf_counter()
+    ot = OracleSolveTiming(pr, args.ref_sample)
     for _ in range(args.warmup):
-        oracle_sample(pr, sw, min(n_sample, 20000), 1)
-    vals = []
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        vals.append(oracle_sample(pr, sw, n_sample, 1)["value"])
-    wall = time.perf_counter() - t0
-    v = statistics.median(vals)
+        ot.step(1)
+    step_s = [ot.step(1) for _ in range(args.steps)]
+    wall = time.perf_counter() - t_wall
+    v = 1.0 / ot.solve_seconds()
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_desc(pr), "sample_points": n_sample, "sweeps_per_solve": sw},
-            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                             "sample": "oracle Phi'(Phi v) on %d points per step, scaled to %d points x %.0f sweeps"
-                                       % (n_sample, pr.n, sw)},
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * statistics.mean(step_s),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_desc(pr),
+                       "step": ("one oracle MG-PCG iteration at the full K" if ot.kind == "tier2"
+                                else "one oracle direct solve")},
+            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": ot.describe(),
+                             **ot.info},
             "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": wall}
     print(json.dumps(line), flush=True)
@@ -265,24 +366,33 @@ def run_ours(args, pr):
     apply64 = time_apply(lambda h, g, v, u: B.sps_apply(h, g, B.SPS_PREC_FP64, v, u))
     point64 = time_apply(lambda h, g, v, u: B.sps_point_apply(h, g, B.SPS_PREC_FP64, v, u))
 
+    # ---- FMA peaks of this GPU at run-time clocks (the library's probe) and their derivation
+    props = torch.cuda.get_device_properties(dev)
+    fma64 = B.sps_probe_fma_rate(fp64=True)
+    fma32 = B.sps_probe_fma_rate(fp64=False)
+    mhz = clk.get("sm_mhz") or 2070.0
+    probe = {"sms": props.multi_processor_count, "sm_mhz_median": mhz,
+             "fp64_fma_per_sm_per_clock": fma64 / (props.multi_processor_count * mhz * 1e6),
+             "fp32_fma_per_sm_per_clock": fma32 / (props.multi_processor_count * mhz * 1e6),
+             "how": "sps_probe_fma_rate: 8 independent FMA chains per thread, 256 threads x 8 CTAs per SM, "
+                    "CUDA events; rate / (SMs x median SM clock during the timed steps)"}
+
     # ---- roofline of the dominant kernel (point operator, apply mode), timed inside the steps
     fma_pt = 2 * 4 ** pr.P                       # gather + scatter multiply-adds per point
     flops_launch = 2.0 * fma_pt * pr.n
     avg_ms = point_ms / max(point_launches, 1)
     fp64_kernel = not mixed
-    fma_rate = B.sps_probe_fma_rate(fp64=fp64_kernel)
     achieved = flops_launch / (avg_ms * 1e-3) / 1e12
-    peak = 2.0 * fma_rate / 1e12
-    # DRAM bytes (read + write) of one FP64 apply-mode launch on this workload, from one ncu
-    # capture of the current kernel (profiles/k_point_fp64_p3_n64_1e6pts.md); None for others
+    peak = 2.0 * (fma64 if fp64_kernel else fma32) / 1e12
     tuning = [list(B.sps_get_tuning(plan.h, g)) for g in range(1, pr.levels + 1)]
-    traffic = POINT_F64_TRAFFIC_BYTES if (fp64_kernel and pr.name == "scale" and pr.n == 1_000_000
-                                          and tuning[-1] == POINT_F64_TRAFFIC_SHAPE) else None
+    cap = point_traffic("fp64" if fp64_kernel else "fp32", pr, tuning[-1])
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "k_point (apply mode), %s" % ("FP64" if fp64_kernel else "FP32/FP64 mix"),
+                "traffic": cap["bytes"] if cap else None, "kernel": "k_point (apply mode), %s" % (
+                    "FP64" if fp64_kernel else "FP32"),
                 "flops_per_launch": flops_launch, "avg_launch_ms": avg_ms, "launches": point_launches,
-                "peak_source": "measured %s FMA probe (sps_probe_fma_rate) x 2 flops at run-time clocks"
-                               % ("FP64" if fp64_kernel else "FP32")}
+                "peak_source": "measured %s FMA probe x 2 flops at run-time clocks (not in MEASURED_PEAKS.json)"
+                               % ("FP64" if fp64_kernel else "FP32"),
+                "traffic_source": cap["source"] if cap else "no ncu capture of this kernel and launch shape"}
 
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": max_ms / args.steps, "higher_is_better": True,
@@ -292,7 +402,11 @@ def run_ours(args, pr):
             "iterations": res.iterations, "rel_res_true": res.rel_res_true, "fp64_applies": res.fp64_applies,
             "operator_gpoint_applies_per_s": {"fp64_apply": pr.n / (apply64 * 1e-3) / 1e9,
                                               "fp64_point_only": pr.n / (point64 * 1e-3) / 1e9},
-            "point_launch_shape": tuning, "roofline": roofline, "clocks": clk, "gpu_launches": launches, "step_ms": step_ms}
+            "point_launch_shape": tuning, "roofline": roofline, "fma_probe": probe, "clocks": clk,
+            "gpu_launches": launches, "step_ms": step_ms}
+    gold = golden_alpha(pr)
+    if gold is not None:
+        line["coef_rel_err_vs_oracle"] = coef_error(coef, gold)
 
     if not mixed:
         point32 = time_apply(lambda h, g, v, u: B.sps_point_apply(h, g, B.SPS_PREC_MIXED, v, u))
@@ -303,13 +417,13 @@ def run_ours(args, pr):
         with B.Plan(pr.P, pr.intervals, pr.levels, pr.lam, pr.lo, pr.hi, precision=B.SPS_PREC_MIXED,
                     autotune=1) as pm:
             cm = torch.zeros(plan.K, dtype=torch.float64, device=dev)
-            for _ in range(1):
-                pm.set_points(x_d, y_d)
-                _, rm = pm.solve(pr.tol, cm)
+            pm.set_points(x_d, y_d)
+            _, rm = pm.solve(pr.tol, cm)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             tm = 0.0
             mixed_steps = max(1, min(args.steps, 3))
+            B.sps_profile_begin()
             for _ in range(mixed_steps):
                 flush.fill_(2.0)
                 e0.record(stream)
@@ -318,33 +432,59 @@ def run_ours(args, pr):
                 e1.record(stream)
                 e1.synchronize()
                 tm += e0.elapsed_time(e1)
-            err = float((cm - coef).abs().max() / coef.abs().max())
-            line["mixed_precision"] = {"solves_per_s": mixed_steps / (tm * 1e-3), "iterations": rm.iterations,
-                                       "fp64_applies": rm.fp64_applies, "rel_res_true": rm.rel_res_true,
-                                       "coef_rel_err_vs_fp64": err}
+            p32_ms, p32_n = B.sps_profile_end()
+            shape32 = list(B.sps_get_tuning(pm.h, pr.levels))
+        mp = {"solves_per_s": mixed_steps / (tm * 1e-3), "iterations": rm.iterations,
+              "fp64_applies": rm.fp64_applies, "rel_res_true": rm.rel_res_true,
+              "coef_rel_err_vs_fp64_gpu": float((cm - coef).abs().max() / coef.abs().max())}
+        if gold is not None:
+            mp["coef_rel_err_vs_oracle"] = coef_error(cm, gold)
+        line["mixed_precision"] = mp
+        # FP32 point operator inside the mixed solves: the slower of streaming its algorithmic
+        # bytes at the measured HBM copy bandwidth and its multiply-adds at the FP32 FMA peak
+        avg32 = p32_ms / max(p32_n, 1)
+        bytes32 = pr.n * pr.P * 4 + 2 * 4 * plan.K
+        t_hbm = bytes32 / (HBM_GBS * 1e9)
+        t_alu = flops_launch / (2.0 * fma32)
+        cap32 = point_traffic("fp32", pr, shape32)
+        line["roofline_fp32"] = {
+            "bound": "alu" if t_alu >= t_hbm else "hbm", "achieved": flops_launch / (avg32 * 1e-3) / 1e12,
+            "peak": 2.0 * fma32 / 1e12, "unit": "TFLOP/s", "frac": max(t_alu, t_hbm) / (avg32 * 1e-3),
+            "hbm_achieved_gbs": bytes32 / (avg32 * 1e-3) / 1e9, "hbm_peak_gbs": HBM_GBS,
+            "algorithmic_bytes_per_launch": bytes32, "traffic": cap32["bytes"] if cap32 else None,
+            "kernel": "k_point (apply mode), FP32, in the mixed solves", "avg_launch_ms": avg32,
+            "launches": p32_n, "launch_shape": shape32,
+            "frac_definition": "max(t_alu, t_hbm) / measured time: t_alu = 2 (q+1)^P FMA per point at the "
+                               "FP32 probe peak, t_hbm = P*4 B per point + 2*4 B per coefficient at the "
+                               "measured HBM copy bandwidth"}
 
-    # ---- end to end through the C ABI with pinned host buffers
+    # ---- end to end through the C ABI with pinned host buffers (copies inside the timed region)
     xh = torch.from_numpy(np.ascontiguousarray(pr.x)).pin_memory()
     yh = torch.from_numpy(np.ascontiguousarray(pr.y)).pin_memory()
     ch = torch.zeros(plan.K, dtype=torch.float64).pin_memory()
     xn, yn, cn = xh.numpy(), yh.numpy(), ch.numpy()
     torch.cuda.synchronize()
     barrier()
-    e2e_steps = max(1, min(args.steps, 2))
-    t0 = time.perf_counter()
+    e2e_steps = max(3, min(args.steps, 5))
+    e2e_s = 0.0
     for _ in range(e2e_steps):
+        flush.fill_(3.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         plan.set_points(xn, yn)
         plan.solve(pr.tol, cn)
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
+        e2e_s += time.perf_counter() - t0
     e2e_rate, _ = replicas.job_rate(e2e_steps, e2e_s, world, dev)
     line["e2e"] = {"value": e2e_rate, "unit": "solves/s", "steps": e2e_steps,
-                   "h2d_bytes_per_step": int(xn.nbytes + yn.nbytes), "d2h_bytes_per_step": int(cn.nbytes)}
+                   "h2d_bytes_per_step": int(xn.nbytes + yn.nbytes), "d2h_bytes_per_step": int(cn.nbytes),
+                   "timing": "host clock around sps_set_points (host x, y) + sps_solve (host coef), "
+                             "L2 flushed before each step"}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        sw = sweeps_per_solve(res.iterations, pr.levels)
-        line["cpu_baseline"] = oracle_sample(pr, sw, min(pr.n, args.ref_sample), 2)
-        line["cpu_baseline"].pop("sweep_s_full", None)
+        ot = OracleSolveTiming(pr, args.cpu_sample)
+        ot.step(3)
+        line["cpu_baseline"] = {"value": 1.0 / ot.solve_seconds(), "unit": "solves/s", "cores": 1,
+                                "kind": "oracle", "sample": ot.describe(), **ot.info}
     plan.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -635,9 +775,10 @@ def main():
     ap.add_argument("--n", type=int, default=None, help="override the number of points")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default=None,
                     help="override the workload's solver precision (--launch-profile, --apply-only)")
-    ap.add_argument("--ref-sample", type=int, default=200_000)
-    ap.add_argument("--ref-iters", type=int, default=0,
-                    help="iterations assumed by the reference arm (0: the workload's MG-PCG count)")
+    ap.add_argument("--ref-sample", type=int, default=100_000,
+                    help="points on which the reference arm times the oracle's set-up")
+    ap.add_argument("--cpu-sample", type=int, default=50_000,
+                    help="points on which cpu_baseline times the oracle's set-up")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.config == "batched":

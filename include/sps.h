@@ -59,13 +59,17 @@ extern "C" {
 #define SPS_ETIMEOUT     -7  /* a device-side loop hit its iteration cap */
 #define SPS_ECUDA        -8  /* a CUDA runtime call failed */
 #define SPS_EEMPTY       -9  /* no data points (n = 0) */
+#define SPS_EINTERNAL   -10  /* a kernel found its launch inconsistent with its input
+                                (a library bug) and skipped work; results are invalid */
 
 /* ---- enums ---- */
 #define SPS_F32 0            /* float  inputs */
 #define SPS_F64 1            /* double inputs */
 #define SPS_MEM_HOST   0
 #define SPS_MEM_DEVICE 1
-#define SPS_PREC_FP64  0     /* every step in FP64 (plain method) */
+#define SPS_PREC_FP64  0     /* every step in FP64 (plain method): basis values,
+                                products, sums, the assembled coarse and
+                                intermediate-level matrices, the coarse solve */
 #define SPS_PREC_MIXED 1     /* FP32 V-cycle and FP32 point operator inside an FP64
                                 flexible PCG with FP64 residual replacement */
 
@@ -110,6 +114,19 @@ typedef struct sps_options {
                               16 sums each) or 3 (4^(P-3) lanes, 64 sums);
                               0 (default): FP32 2 for P = 3, else 3.  Ignored
                               for other P; the autotuner may change it */
+    int    coarse_cg;      /* coarse grid solver on level 1 (Section 3.2, coarse grid
+                              solver): 0 (default) the dense inverse of the assembled
+                              A_1, formed from its Jacobi-scaled form (K_1 <= 4096);
+                              1 an inner matrix-free Jacobi-preconditioned CG on A_1
+                              (no assembly, no K_1 limit), run for coarse_iters
+                              iterations per coarse solve.  The inner CG makes the
+                              V-cycle a nonlinear preconditioner, so the outer
+                              iteration then uses the flexible (Polak-Ribiere) beta */
+    int    coarse_iters;   /* inner CG iterations per coarse solve (default 32) */
+    int64_t max_device_bytes; /* 0 (default): no limit; else the plan's device memory
+                              (plan buffers, point data and call temporaries) may not
+                              exceed this many bytes: an allocation beyond it fails
+                              with SPS_ENOMEM before cudaMalloc is called */
 } sps_options;
 
 typedef struct sps_result {
@@ -130,9 +147,13 @@ SPS_API void sps_default_options(sps_options* opt);
  *  lo, hi [P]:   domain Omega = prod [lo_p, hi_p] (NULL -> 0 and 1).
  *  levels:       number of grid levels G >= 1 (Section 3.2, hierarchy); the
  *                coarsest has K_1 = prod (N_p / 2^(G-1) + 3) <= 4096 coefficients
- *                (it is solved densely), and P * log2(max_p N_p) <= 26.
+ *                when it is solved densely (sps_options.coarse_cg = 0), and
+ *                P * log2(max_p N_p) <= 26.
  *  lambda:       smoothing parameter >= 0 (0 gives the least-squares spline,
- *                which is SPD only when every basis support holds enough data).
+ *                which is SPD only when every basis support holds enough data;
+ *                otherwise the solve reports SPS_EBREAKDOWN).
+ *  q:            the spline degree; only cubic splines (q = 3) are built, the
+ *                degree of every workload here (any other q: SPS_EINVAL).
  *  opt:          NULL for defaults.
  * Allocates the per-level coefficient vectors on the current CUDA device.
  * Errors: SPS_EINVAL, SPS_ENOMEM, SPS_ECUDA. */
@@ -140,13 +161,17 @@ SPS_API int sps_plan_create(sps_plan** out, int P, int q, const int* intervals, 
                     const double* hi, int levels, double lambda, const sps_options* opt);
 
 /* Load the data (x_i, y_i), i < n: copies them to the device, validates that
- * every coordinate is finite and inside [lo_p, hi_p], sorts the points by the
+ * every coordinate is finite and inside [lo_p, hi_p] and every response is
+ * finite, sorts the points by the
  * Morton key of their finest knot cell (stable), builds the per-level work
  * lists, computes diag(A_g) (Algorithm 5 plus the penalty diagonal), the
  * right-hand side Phi'y (Algorithm 3), the coarse matrix and its inverse, and
  * omega.  x: n x P row-major, y: n, both of `dtype`, in `mem`.
  * The caller may free x and y once the call returns.  Synchronises `stream`.
- * Errors: SPS_EINVAL, SPS_EEMPTY (n == 0), SPS_EDOM, SPS_ENOMEM, SPS_ECUDA. */
+ * Errors: SPS_EINVAL, SPS_EEMPTY (n == 0), SPS_EDOM (a coordinate outside the
+ * domain, or a coordinate or response not finite), SPS_ENOMEM, SPS_EBREAKDOWN
+ * (the power iteration for omega found no positive eigenvalue), SPS_ECUDA,
+ * SPS_EINTERNAL. */
 SPS_API int sps_set_points(sps_plan* plan, int64_t n, const void* x, const void* y, int dtype, int mem,
                    void* stream);
 
@@ -154,7 +179,10 @@ SPS_API int sps_set_points(sps_plan* plan, int64_t n, const void* x, const void*
  * Algorithm 8 (FP64) or its mixed-precision flexible variant.  coef: K_G
  * doubles in `mem` (input = initial guess when opt.warm_start; output = alpha).
  * res may be NULL.  Synchronises `stream`.
- * Errors: SPS_ESTATE (no points), SPS_EINVAL, SPS_ENOCONV, SPS_EBREAKDOWN, SPS_ECUDA. */
+ * Errors: SPS_ESTATE (no points), SPS_EINVAL, SPS_ENOCONV (max_iter reached,
+ * or a residual that is not finite after the iteration stopped; res is filled
+ * and coef holds the last iterate), SPS_EBREAKDOWN (p'Ap <= 0 or a non-finite
+ * step), SPS_ECUDA, SPS_EINTERNAL. */
 SPS_API int sps_solve(sps_plan* plan, double* coef, int mem, double tol, sps_result* res, void* stream);
 
 /* Change lambda of a plan; takes effect at the next sps_set_points (which
@@ -207,6 +235,11 @@ SPS_API int sps_evaluate(sps_plan* plan, const double* coef, int64_t m, const vo
  * Errors: SPS_EINVAL (NULL or level out of range). */
 SPS_API int sps_get_tuning(const sps_plan* plan, int level, int* tile, int* lanes_r);
 
+/* Device memory the plan holds now, in bytes (its buffers and point data).
+ * Not a step of the paper's method: serving admits requests by it.
+ * Errors: SPS_EINVAL (NULL argument). */
+SPS_API int sps_plan_device_bytes(const sps_plan* plan, int64_t* bytes);
+
 /* ---------------- component entry points (each one step of the solve) ----------------
  * All vectors are doubles in `mem`; `prec` selects the FP64 kernels
  * (SPS_PREC_FP64) or the FP32 kernels of the mixed mode (SPS_PREC_MIXED, inputs
@@ -242,8 +275,24 @@ SPS_API int sps_prolong(sps_plan* plan, int level, int prec, const double* c, do
 /* c = (I_{g-1}^{g})' f (restriction, Section 3.2 grid transfer); f: K_g, c: K_{g-1}. */
 SPS_API int sps_restrict(sps_plan* plan, int level, int prec, const double* f, double* c, int mem, void* stream);
 
-/* e = A_1^{-1} r on the coarsest level (Section 3.2, coarse grid solver). */
+/* e = A_1^{-1} r on the coarsest level (Section 3.2, coarse grid solver), by the
+ * plan's coarse solver (sps_options.coarse_cg).  In FP64 plans the dense path
+ * is the GEMV with the inverse followed by one step of iterative refinement
+ * with the assembled A_1 (FP64 residual). */
 SPS_API int sps_coarse_solve(sps_plan* plan, const double* r, double* e, int mem, void* stream);
+
+/* Assembled operator A_g = Phi_g'Phi_g + lambda Lambda_g of level g as the
+ * solver holds it (Section 3.2, hierarchy; Algorithm 5 for the diagonal):
+ *  g = 1 with the dense coarse solver: the dense K_1 x K_1 matrix, row-major;
+ *  an intermediate level assembled in stencil form (sps_options.hybrid): the
+ *  offset-major stencil out[s * K_g + k] = A_g(k, k + offset_s), s < 7^P, with
+ *  offset_s the base-7 digits of s minus 3 (last dimension fastest); entries
+ *  whose column falls outside the grid are 0.
+ * *entries receives the number of doubles (0 when the level is applied matrix
+ * free; out is then untouched); out may be NULL to query the count.  Values
+ * are those the solver uses (FP64 plans: FP64; mixed plans keep FP32 stencils,
+ * returned widened).  Errors: SPS_ESTATE, SPS_EINVAL. */
+SPS_API int sps_level_matrix(sps_plan* plan, int level, double* out, int64_t* entries, int mem, void* stream);
 
 /* z = one V-cycle (Algorithm 7) from zero applied to r on level G. */
 SPS_API int sps_vcycle(sps_plan* plan, int prec, const double* r, double* z, int mem, void* stream);
@@ -280,13 +329,19 @@ SPS_API int sps_profile_end(double* point_apply_ms, uint64_t* point_apply_launch
  *  (intervals need not be powers of two here); K = prod (N_p + 3) must be
  *  <= SPS_NOALLOC_MAX_COEF, larger grids are rejected with SPS_EINVAL.
  *  v, u: K doubles in DEVICE memory (u is overwritten); stream: cudaStream_t.
+ *  u must not overlap v (SPS_EINVAL).
  * It calls no cudaMalloc, cudaFree or allocating library routine.  All calls
  * share the one scratch array, so calls that overlap on the GPU (other
  * streams or host threads) race; the scratch needs no clearing because every
  * step writes the entries it later reads.  The first call on a device sets up
  * (looks up the scratch address with cudaGetSymbolAddress and uploads the
  * cubic element matrices to constant memory); make that first call before any
- * stream capture.  Errors: SPS_EINVAL, SPS_ECUDA. */
+ * stream capture.  Under CUDA's default lazy module loading the 12 MiB array
+ * is taken on a device at that first call, not when the library loads (with
+ * CUDA_MODULE_LOADING=EAGER: at load): a caller about to hand the GPU's memory
+ * to another allocator makes one call first.  The set-up is not redone after
+ * cudaDeviceReset: do not use the entry point on a device after a reset.
+ * Errors: SPS_EINVAL, SPS_ECUDA. */
 #define SPS_NOALLOC_MAX_COEF 262144
 SPS_API int sps_penalty_apply_noalloc(int P, const int* intervals, const double* lo, const double* hi,
                                       double scale, const double* v, double* u, void* stream);

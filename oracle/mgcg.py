@@ -171,3 +171,13 @@ def mgcg(H: Hierarchy, tol: float, nu1: int = 1, nu2: int = 1, max_iter: int = 5
         it += 1
         hist.append(np.linalg.norm(r) / nb)
     return CGResult(alpha, it, hist[-1], hist)
+
+
+def solve_tier2(x, y, lo, hi, intervals, q, lam, G, tol, omega=None, nu1=1, nu2=1, max_iter=20000) -> CGResult:
+    """alpha* = A^-1 b for problems too large for the banded Cholesky: Algorithm 8
+    on assembled matrices with the Galerkin coarse operators I' A_{g+1} I
+    (Section 3.2, grid transfer), run to |r| <= tol |b| (tol = 1e-13 or below).
+    The coarse operators come from the fine matrix by another route than the
+    rediscretisation that the CUDA path uses; both give A_g in exact arithmetic."""
+    H = build_hierarchy(x, y, lo, hi, intervals, q, lam, G, omega=omega, galerkin=True)
+    return mgcg(H, tol, nu1=nu1, nu2=nu2, max_iter=max_iter)

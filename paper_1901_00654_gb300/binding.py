@@ -17,20 +17,22 @@ import numpy as np
 from . import build as _build
 
 SPS_OK, SPS_EINVAL, SPS_EDOM, SPS_ENOMEM, SPS_ESTATE = 0, -1, -2, -3, -4
-SPS_EBREAKDOWN, SPS_ENOCONV, SPS_ETIMEOUT, SPS_ECUDA, SPS_EEMPTY = -5, -6, -7, -8, -9
+SPS_EBREAKDOWN, SPS_ENOCONV, SPS_ETIMEOUT, SPS_ECUDA, SPS_EEMPTY, SPS_EINTERNAL = -5, -6, -7, -8, -9, -10
 SPS_F32, SPS_F64 = 0, 1
 SPS_MEM_HOST, SPS_MEM_DEVICE = 0, 1
 SPS_PREC_FP64, SPS_PREC_MIXED = 0, 1
 
 ERROR_NAMES = {0: "SPS_OK", -1: "SPS_EINVAL", -2: "SPS_EDOM", -3: "SPS_ENOMEM", -4: "SPS_ESTATE",
-               -5: "SPS_EBREAKDOWN", -6: "SPS_ENOCONV", -7: "SPS_ETIMEOUT", -8: "SPS_ECUDA", -9: "SPS_EEMPTY"}
+               -5: "SPS_EBREAKDOWN", -6: "SPS_ENOCONV", -7: "SPS_ETIMEOUT", -8: "SPS_ECUDA", -9: "SPS_EEMPTY",
+               -10: "SPS_EINTERNAL"}
 
 EXPORTED = ["sps_default_options", "sps_plan_create", "sps_set_points", "sps_solve", "sps_destroy",
             "sps_last_error", "sps_coef_count", "sps_apply", "sps_penalty_apply", "sps_diag", "sps_rhs",
             "sps_prolong", "sps_restrict", "sps_coarse_solve", "sps_vcycle", "sps_get_sort", "sps_get_omega",
             "sps_set_omega", "sps_probe_fma_rate", "sps_point_apply", "sps_launch_count",
             "sps_profile_begin", "sps_profile_end", "sps_solve_batch", "sps_set_lambda",
-            "sps_penalty_apply_noalloc", "sps_get_tuning", "sps_evaluate"]
+            "sps_penalty_apply_noalloc", "sps_get_tuning", "sps_evaluate", "sps_level_matrix",
+            "sps_plan_device_bytes"]
 
 
 class sps_options(C.Structure):
@@ -38,7 +40,8 @@ class sps_options(C.Structure):
                 ("power_iters", C.c_int), ("max_iter", C.c_int), ("warm_start", C.c_int), ("tile", C.c_int),
                 ("replace_ratio", C.c_double), ("hybrid", C.c_int),
                 ("graphs", C.c_int), ("precondition", C.c_int), ("autotune", C.c_int),
-                ("lanes_r", C.c_int)]
+                ("lanes_r", C.c_int), ("coarse_cg", C.c_int), ("coarse_iters", C.c_int),
+                ("max_device_bytes", C.c_int64)]
 
 
 class sps_result(C.Structure):
@@ -88,6 +91,8 @@ def load(path: str | None = None) -> C.CDLL:
         "sps_solve_batch": (I, [C.POINTER(P), I, C.POINTER(P), I, D, C.POINTER(sps_result), P]),
         "sps_set_lambda": (I, [P, D]),
         "sps_penalty_apply_noalloc": (I, [I, C.POINTER(C.c_int), C.POINTER(D), C.POINTER(D), D, P, P, P]),
+        "sps_level_matrix": (I, [P, I, P, C.POINTER(C.c_int64), I, P]),
+        "sps_plan_device_bytes": (I, [P, C.POINTER(C.c_int64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -332,6 +337,25 @@ def sps_get_tuning(plan, level) -> tuple:
 def sps_set_omega(plan, omega) -> None:
     arr = np.ascontiguousarray(omega, dtype=np.float64)
     _check(lib().sps_set_omega(plan, C.c_void_p(arr.ctypes.data)), "sps_set_omega")
+
+
+def sps_plan_device_bytes(plan) -> int:
+    b = C.c_int64()
+    _check(lib().sps_plan_device_bytes(plan, C.byref(b)), "sps_plan_device_bytes")
+    return b.value
+
+
+def sps_level_matrix(plan, level, out=None, stream=None) -> int:
+    """Number of entries of level `level`'s assembled matrix (0: matrix free);
+    with `out` (numpy array or CUDA tensor of that many doubles) also copies them."""
+    cnt = C.c_int64()
+    if out is None:
+        _check(lib().sps_level_matrix(plan, level, None, C.byref(cnt), SPS_MEM_HOST, _stream(stream)),
+               "sps_level_matrix")
+        return cnt.value
+    po, mo = _buf(out)
+    _check(lib().sps_level_matrix(plan, level, po, C.byref(cnt), mo, _stream(stream)), "sps_level_matrix")
+    return cnt.value
 
 
 def sps_probe_fma_rate(fp64: bool, stream=None) -> float:

@@ -31,7 +31,7 @@ namespace {
 
 // scalar slots in plan->scal
 constexpr int S_RZ_A = 0, S_PV = 2, S_RR = 3, S_W = 4, S_FLAG = 6, S_RZ_B = 8, S_TMP = 10, S_TMP2 = 12;
-constexpr int NSCAL = 16;
+constexpr int NSCAL = 32;   // slots 16.. belong to the inner coarse CG (grid_ops.cu)
 
 // ---- exact 1-D Gram matrices of the cubic B-splines --------------------------
 // Piece m of the uniform cubic B-spline on one cell, as monomial coefficients
@@ -83,41 +83,16 @@ void gram_band(int N, double h, int r, double* band) {
     }
 }
 
-template <typename T>
-void free_vecs(LevelVecs<T>& v) {
-  cudaFree(v.alpha);
-  cudaFree(v.b);
-  cudaFree(v.u);
-  cudaFree(v.dinv);
-  cudaFree(v.band);
-  v = LevelVecs<T>();
-}
-
 void free_points(sps_plan* pl) {
-  if (pl->x32_sorted != pl->x_sorted) cudaFree(pl->x32_sorted);
+  if (pl->x32_sorted != pl->x_sorted) pfree(pl, pl->x32_sorted);
   pl->x32_sorted = nullptr;
-  cudaFree(pl->x_sorted);
-  cudaFree(pl->y_sorted);
-  cudaFree(pl->keys);
-  cudaFree(pl->keys_tmp);
-  cudaFree(pl->perm);
-  cudaFree(pl->perm_tmp);
-  pl->x_sorted = nullptr;
-  pl->y_sorted = nullptr;
-  pl->keys = pl->keys_tmp = nullptr;
-  pl->perm = pl->perm_tmp = nullptr;
+  pfree(pl, pl->x_sorted);
+  pfree(pl, pl->y_sorted);
+  pfree(pl, pl->keys);
+  pfree(pl, pl->keys_tmp);
+  pfree(pl, pl->perm);
+  pfree(pl, pl->perm_tmp);
   pl->n_cap = 0;
-}
-
-template <typename T>
-int alloc(T** p, long long count) {
-  if (count < 1) count = 1;
-  if (cudaMalloc((void**)p, sizeof(T) * count) != cudaSuccess) {
-    cudaGetLastError();
-    set_error("device allocation failed");
-    return SPS_ENOMEM;
-  }
-  return SPS_OK;
 }
 
 
@@ -194,6 +169,46 @@ int copy_out(double* dst, const double* src, long long n, int mem, cudaStream_t 
 
 }  // namespace
 
+// ---- device memory of a plan ----------------------------------------------------
+int plan_alloc(sps_plan* pl, void** p, size_t bytes) {
+  *p = nullptr;
+  if (pl->opt.max_device_bytes > 0 && pl->dev_bytes + (long long)bytes > (long long)pl->opt.max_device_bytes) {
+    set_error("the plan's device memory limit (sps_options.max_device_bytes) would be exceeded");
+    return SPS_ENOMEM;
+  }
+  if (cudaMalloc(p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    set_error("device allocation failed");
+    return SPS_ENOMEM;
+  }
+  pl->dev_sizes[*p] = bytes;
+  pl->dev_bytes += (long long)bytes;
+  return SPS_OK;
+}
+
+void plan_free(sps_plan* pl, void* p) {
+  if (!p) return;
+  auto it = pl->dev_sizes.find(p);
+  if (it != pl->dev_sizes.end()) {
+    pl->dev_bytes -= (long long)it->second;
+    pl->dev_sizes.erase(it);
+  }
+  cudaFree(p);
+}
+
+int check_device_errors(sps_plan* pl, cudaStream_t st) {
+  int flags = 0;
+  SPS_CUDA(cudaMemcpyAsync(&flags, pl->err_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SPS_CUDA(cudaStreamSynchronize(st));
+  if (flags & ERR_SMEM) {
+    SPS_CUDA(cudaMemsetAsync(pl->err_flag, 0, sizeof(int), st));
+    set_error("internal error: the point operator's staged points exceeded its shared memory (work skipped)");
+    return SPS_EINTERNAL;
+  }
+  return SPS_OK;
+}
+
 // ---- operator on one level: u = (Phi_g'Phi_g + lambda Lambda_g) v --------------
 template <typename T>
 int apply_level(sps_plan* pl, int g, const T* v, T* u, cudaStream_t st) {
@@ -231,7 +246,13 @@ int vcycle_into(sps_plan* pl, const T* bG, T* xG, cudaStream_t st) {
     }
     SPS_TRY(restrict_res<T>(pl, g, V.u, B(g), B(g - 1), st));         // b_{g-1} = I'(A alpha - b)
   }
-  SPS_TRY(coarse_solve<T>(pl, B(1), X(1), st));                       // e = A_1^{-1} r
+  if (pl->opt.coarse_cg) {                                            // e ~ A_1^{-1} r by inner CG
+    T* t6 = sizeof(T) == 8 ? (T*)pl->dtmp[6] : (T*)pl->ftmp[6];
+    T* t7 = sizeof(T) == 8 ? (T*)pl->dtmp[7] : (T*)pl->ftmp[7];
+    SPS_TRY(coarse_cg<T>(pl, B(1), X(1), t6, t7, st));
+  } else {
+    SPS_TRY(coarse_solve<T>(pl, B(1), X(1), st));                     // e = A_1^{-1} r
+  }
   for (int g = 2; g <= G; ++g) {
     Level& L = pl->lev[g - 1];
     LevelVecs<T>& V = vecs<T>(L);
@@ -314,19 +335,16 @@ int assemble_coarse_levels(sps_plan* pl, cudaStream_t st) {
     const double sweep_s = (double)pl->n * 2.0 * loc / (0.3 * rate);
     const bool want = spmv_s < sweep_s && (double)S * K * 8.0 <= 8e9;
     if (!want) {
-      cudaFree(L.st_d);
-      cudaFree(L.st_f);
-      L.st_d = nullptr;
-      L.st_f = nullptr;
+      pfree(pl, L.st_d);
+      pfree(pl, L.st_f);
       continue;
     }
     L.S = (int)S;
-    if (!L.st_d) SPS_TRY(alloc(&L.st_d, S * K));
-    if (mixed && !L.st_f) SPS_TRY(alloc(&L.st_f, S * K));
+    if (!L.st_d) SPS_TRY(palloc(pl, &L.st_d, S * K));
+    if (mixed && !L.st_f) SPS_TRY(palloc(pl, &L.st_f, S * K));
     SPS_TRY(stencil_assemble(pl, g, st));
     if (mixed) {   // the FP32 V-cycle reads the FP32 copy only
-      cudaFree(L.st_d);
-      L.st_d = nullptr;
+      pfree(pl, L.st_d);
     }
   }
   return SPS_OK;
@@ -426,15 +444,21 @@ int solve_fp64(sps_plan* pl, double tol, sps_result* res, bool warm, cudaStream_
   auto half_apply = [&](cudaStream_t s) -> int {
     SPS_TRY(apply_level<double>(pl, G, pl->p, pl->v, s));
     SPS_TRY(dot(pl, pl->p, pl->v, K, S_PV, s));
+    if (pl->opt.precondition && pl->opt.coarse_cg)   // r_prev for the flexible beta
+      SPS_CUDA(cudaMemcpyAsync(pl->rprev, pl->r, sizeof(double) * K, cudaMemcpyDeviceToDevice, s));
     SPS_TRY(pcg_update_xr(pl, K, S_RZ_A, s));
     SPS_CUDA(cudaMemcpyAsync(pl->host_scal, pl->scal, sizeof(double) * NSCAL, cudaMemcpyDeviceToHost, s));
     return SPS_OK;
   };
-  // z = V(r); beta = r'z / r~'z~; p = z + beta p; then the next half_apply
+  // z = V(r); beta = r'z / r~'z~ (Algorithm 8), or z'(r - r~) / r~'z~ (flexible,
+  // when the inner coarse CG makes the V-cycle nonlinear); p = z + beta p;
+  // then the next half_apply
+  const bool flexible = pl->opt.precondition && pl->opt.coarse_cg;
   auto body = [&](cudaStream_t s) -> int {
     SPS_TRY(precondition64(s));
-    SPS_TRY(dot(pl, pl->r, pl->z, K, S_RZ_B, s));
-    SPS_TRY(pcg_update_p(pl, K, S_RZ_B, S_RZ_A, 0, s));
+    if (flexible) SPS_TRY(dot2(pl, pl->z, pl->r, pl->rprev, K, S_RZ_B, s));   // z'r, z'r_prev
+    else SPS_TRY(dot(pl, pl->r, pl->z, K, S_RZ_B, s));
+    SPS_TRY(pcg_update_p(pl, K, S_RZ_B, S_RZ_A, flexible ? 1 : 0, s));
     SPS_CUDA(cudaMemcpyAsync(pl->scal + S_RZ_A, pl->scal + S_RZ_B, sizeof(double), cudaMemcpyDeviceToDevice, s));
     return half_apply(s);
   };
@@ -442,7 +466,8 @@ int solve_fp64(sps_plan* pl, double tol, sps_result* res, bool warm, cudaStream_
   SPS_TRY(restart(warm));
   for (int round = 0; round < 4; ++round) {
     bool first = true;
-    while (rel > tol && it < pl->opt.max_iter) {
+    // !(rel <= tol): a non-finite residual does not count as converged
+    while (!(rel <= tol) && std::isfinite(rel) && it < pl->opt.max_iter) {
       if (first) {
         SPS_TRY(half_apply(st));
         SPS_CUDA(cudaStreamSynchronize(st));
@@ -464,12 +489,12 @@ int solve_fp64(sps_plan* pl, double tol, sps_result* res, bool warm, cudaStream_
     SPS_TRY(vec_residual(pl->z, pl->rhs, pl->v, K, pl->scal, S_TMP, pl, st));
     SPS_TRY(read_scalars(pl, st));
     res->rel_res_true = std::sqrt(pl->host_scal[S_TMP]) / nb;
-    if (res->rel_res_true <= tol || it >= pl->opt.max_iter) break;
+    if (res->rel_res_true <= tol || it >= pl->opt.max_iter || !std::isfinite(res->rel_res_true)) break;
     SPS_TRY(restart(true));
   }
   res->iterations = it;
   res->rel_res = rel;
-  if (status == SPS_OK && res->rel_res_true > tol) status = SPS_ENOCONV;
+  if (status == SPS_OK && !(res->rel_res_true <= tol)) status = SPS_ENOCONV;
   res->status = status;
   return status;
 }
@@ -532,7 +557,7 @@ int solve_mixed(sps_plan* pl, double tol, sps_result* res, bool warm, cudaStream
   rel = std::sqrt(pl->host_scal[S_RR]) / nb;
   rlast = std::sqrt(pl->host_scal[S_RR]);
   bool restarted = true;   // the next step is a half_apply (after the first V-cycle or a replacement)
-  while (rel > tol && it < pl->opt.max_iter) {
+  while (!(rel <= tol) && std::isfinite(rel) && it < pl->opt.max_iter) {
     if (restarted) {
       SPS_TRY(half_apply(st));
       SPS_CUDA(cudaStreamSynchronize(st));
@@ -575,15 +600,17 @@ int solve_mixed(sps_plan* pl, double tol, sps_result* res, bool warm, cudaStream
   SPS_TRY(vec_residual(pl->z, pl->rhs, pl->v, K, pl->scal, S_TMP, pl, st));
   SPS_TRY(read_scalars(pl, st));
   res->rel_res_true = std::sqrt(pl->host_scal[S_TMP]) / nb;
-  if (status == SPS_OK && res->rel_res_true > tol) status = SPS_ENOCONV;
+  if (status == SPS_OK && !(res->rel_res_true <= tol)) status = SPS_ENOCONV;
   res->status = status;
   return status;
 }
 
-// Temporary device copies of double vectors for the component entry points.
+// Temporary device buffers of a call (counted against the plan's limit while held).
 struct DevBuf {
+  sps_plan* pl;
   void* p = nullptr;
-  ~DevBuf() { if (p) cudaFree(p); }
+  explicit DevBuf(sps_plan* plan) : pl(plan) {}
+  ~DevBuf() { plan_free(pl, p); }
 };
 
 int stage_in(const double* src, long long n, int mem, DevBuf& buf, const double** dev, cudaStream_t st) {
@@ -591,7 +618,7 @@ int stage_in(const double* src, long long n, int mem, DevBuf& buf, const double*
     *dev = src;
     return SPS_OK;
   }
-  SPS_TRY(alloc((double**)&buf.p, n));
+  SPS_TRY(palloc(buf.pl, (double**)&buf.p, n));
   SPS_CUDA(cudaMemcpyAsync(buf.p, src, sizeof(double) * n, cudaMemcpyHostToDevice, st));
   *dev = (const double*)buf.p;
   return SPS_OK;
@@ -602,7 +629,7 @@ int stage_out_ptr(double* dst, long long n, int mem, DevBuf& buf, double** dev) 
     *dev = dst;
     return SPS_OK;
   }
-  SPS_TRY(alloc((double**)&buf.p, n));
+  SPS_TRY(palloc(buf.pl, (double**)&buf.p, n));
   *dev = (double*)buf.p;
   return SPS_OK;
 }
@@ -622,10 +649,10 @@ int check_level(const sps_plan* pl, int level, int lowest) {
 
 // Run a float kernel on double inputs: widen/narrow through temporaries.
 template <typename F>
-int run_f32(long long nin, long long nout, const double* in, double* out, F&& fn, cudaStream_t st) {
-  DevBuf a, b;
-  SPS_TRY(alloc((float**)&a.p, nin));
-  SPS_TRY(alloc((float**)&b.p, nout));
+int run_f32(sps_plan* pl, long long nin, long long nout, const double* in, double* out, F&& fn, cudaStream_t st) {
+  DevBuf a(pl), b(pl);
+  SPS_TRY(palloc(pl, (float**)&a.p, nin));
+  SPS_TRY(palloc(pl, (float**)&b.p, nout));
   SPS_TRY(vec_cast_d2f((float*)a.p, in, nin, st));
   SPS_TRY(fn((const float*)a.p, (float*)b.p));
   SPS_TRY(vec_cast_f2d(out, (const float*)b.p, nout, st));
@@ -673,6 +700,9 @@ void sps_default_options(sps_options* opt) {
   opt->precondition = 1;
   opt->autotune = 0;
   opt->lanes_r = 0;
+  opt->coarse_cg = 0;
+  opt->coarse_iters = 32;
+  opt->max_device_bytes = 0;
 }
 
 const char* sps_last_error(void) { return g_last_error.c_str(); }
@@ -705,7 +735,9 @@ int sps_plan_create(sps_plan** out, int P, int q, const int* intervals, const do
   if (opt) o = *opt;
   if (o.nu1 < 0 || o.nu2 < 0 || o.max_iter < 1 || (o.precision != SPS_PREC_FP64 && o.precision != SPS_PREC_MIXED) ||
       o.tile < 0 || (o.tile & (o.tile - 1)) != 0 || (o.autotune != 0 && o.autotune != 1) ||
-      (o.lanes_r != 0 && o.lanes_r != 2 && o.lanes_r != 3)) {
+      (o.lanes_r != 0 && o.lanes_r != 2 && o.lanes_r != 3) || (o.coarse_cg != 0 && o.coarse_cg != 1) ||
+      o.coarse_iters < 1 || o.coarse_iters > 100000 || o.max_device_bytes < 0 || !(o.omega >= 0.0 || o.omega <= 0.0) ||
+      (o.replace_ratio != 0.0 && !(o.replace_ratio > 0.0 && o.replace_ratio < 1.0))) {
     set_error("invalid options");
     return SPS_EINVAL;
   }
@@ -769,8 +801,8 @@ int sps_plan_create(sps_plan** out, int P, int q, const int* intervals, const do
     }
     level_tile(G, G.ts);
     pl->lev[g - 1].lanes_r = (P == 3 || P == 4) ? o.lanes_r : 0;
-    if (g == 1 && G.K > COARSE_MAX) {
-      set_error("coarsest level too large for the dense coarse solve (K_1 > 4096): add levels");
+    if (g == 1 && G.K > COARSE_MAX && !o.coarse_cg) {
+      set_error("coarsest level too large for the dense coarse solve (K_1 > 4096): add levels or use coarse_cg");
       rc = SPS_EINVAL;
     }
     if ((long long)G.patch * 8 * 2 > 200 * 1024) {
@@ -797,10 +829,10 @@ int sps_plan_create(sps_plan** out, int P, int q, const int* intervals, const do
       off += 3LL * G.J[p] * BAND;
     }
     std::vector<float> hf(hb.begin(), hb.end());
-    if ((rc = alloc(&L.d.alpha, G.K)) || (rc = alloc(&L.d.b, G.K)) || (rc = alloc(&L.d.u, G.K)) ||
-        (rc = alloc(&L.d.dinv, G.K)) || (rc = alloc(&L.d.band, nb)) || (rc = alloc(&L.f.alpha, G.K)) ||
-        (rc = alloc(&L.f.b, G.K)) || (rc = alloc(&L.f.u, G.K)) || (rc = alloc(&L.f.dinv, G.K)) ||
-        (rc = alloc(&L.f.band, nb)) || (rc = alloc(&L.diag, G.K)))
+    if ((rc = palloc(pl, &L.d.alpha, G.K)) || (rc = palloc(pl, &L.d.b, G.K)) || (rc = palloc(pl, &L.d.u, G.K)) ||
+        (rc = palloc(pl, &L.d.dinv, G.K)) || (rc = palloc(pl, &L.d.band, nb)) || (rc = palloc(pl, &L.f.alpha, G.K)) ||
+        (rc = palloc(pl, &L.f.b, G.K)) || (rc = palloc(pl, &L.f.u, G.K)) || (rc = palloc(pl, &L.f.dinv, G.K)) ||
+        (rc = palloc(pl, &L.f.band, nb)) || (rc = palloc(pl, &L.diag, G.K)))
       break;
     if (cudaMemcpy(L.d.band, hb.data(), sizeof(double) * nb, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(L.f.band, hf.data(), sizeof(float) * nb, cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -812,19 +844,23 @@ int sps_plan_create(sps_plan** out, int P, int q, const int* intervals, const do
   const long long K1 = pl->lev[0].geom.K;
   const long long Km = max_K(pl);
   for (int i = 0; i < 8 && rc == SPS_OK; ++i) {
-    rc = alloc(&pl->dtmp[i], Km);
-    if (rc == SPS_OK) rc = alloc(&pl->ftmp[i], Km);
+    rc = palloc(pl, &pl->dtmp[i], Km);
+    if (rc == SPS_OK) rc = palloc(pl, &pl->ftmp[i], Km);
   }
   if (rc == SPS_OK)
-    if ((rc = alloc(&pl->x, KG)) || (rc = alloc(&pl->r, KG)) || (rc = alloc(&pl->z, KG)) ||
-        (rc = alloc(&pl->p, KG)) || (rc = alloc(&pl->v, KG)) || (rc = alloc(&pl->rprev, KG)) ||
-        (rc = alloc(&pl->p32, KG)) || (rc = alloc(&pl->rhs, KG)) || (rc = alloc(&pl->coarse_inv, K1 * K1)) ||
-        (rc = alloc(&pl->coarse_inv_f, K1 * K1)) || (rc = alloc(&pl->coarse_tmp, 4 * K1)) ||
-        (rc = alloc(&pl->scal, NSCAL)) || (rc = alloc(&pl->red_part, 4 * 304)) ||
-        (rc = alloc(&pl->red_count, 1)) || (rc = alloc(&pl->err_flag, 1))) {
+    if ((rc = palloc(pl, &pl->x, KG)) || (rc = palloc(pl, &pl->r, KG)) || (rc = palloc(pl, &pl->z, KG)) ||
+        (rc = palloc(pl, &pl->p, KG)) || (rc = palloc(pl, &pl->v, KG)) || (rc = palloc(pl, &pl->rprev, KG)) ||
+        (rc = palloc(pl, &pl->p32, KG)) || (rc = palloc(pl, &pl->rhs, KG)) ||
+        (rc = palloc(pl, &pl->scal, NSCAL)) || (rc = palloc(pl, &pl->red_part, 4 * 304)) ||
+        (rc = palloc(pl, &pl->red_count, 1)) || (rc = palloc(pl, &pl->err_flag, 1))) {
+    }
+  if (rc == SPS_OK && !o.coarse_cg)
+    if ((rc = palloc(pl, &pl->coarse_A, K1 * K1)) || (rc = palloc(pl, &pl->coarse_inv, K1 * K1)) ||
+        (rc = palloc(pl, &pl->coarse_invt, K1 * K1)) || (rc = palloc(pl, &pl->coarse_tmp, 6 * K1 + K1 * K1))) {
     }
   if (rc == SPS_OK) {
     if (cudaMemset(pl->red_count, 0, sizeof(unsigned int)) != cudaSuccess ||
+        cudaMemset(pl->err_flag, 0, sizeof(int)) != cudaSuccess ||
         cudaMallocHost((void**)&pl->host_scal, sizeof(double) * NSCAL) != cudaSuccess) {
       set_error("initialisation failed");
       rc = SPS_ECUDA;
@@ -851,42 +887,10 @@ int sps_set_lambda(sps_plan* pl, double lambda) {
 
 int sps_destroy(sps_plan* pl) {
   if (!pl) return SPS_OK;
-  for (int g = 0; g < MAXL; ++g) {
-    Level& L = pl->lev[g];
-    free_vecs(L.d);
-    free_vecs(L.f);
-    cudaFree(L.diag);
-    cudaFree(L.st_d);
-    cudaFree(L.st_f);
-    cudaFree(L.pre);
-    cudaFree(L.pre2);
-    cudaFree(L.run_begin);
-    cudaFree(L.run_cell);
-    cudaFree(L.run_order);
-    cudaFree(L.items);
-  }
-  free_points(pl);
-  for (int i = 0; i < 8; ++i) {
-    cudaFree(pl->dtmp[i]);
-    cudaFree(pl->ftmp[i]);
-  }
-  cudaFree(pl->x);
-  cudaFree(pl->r);
-  cudaFree(pl->z);
-  cudaFree(pl->p);
-  cudaFree(pl->v);
-  cudaFree(pl->rprev);
-  cudaFree(pl->p32);
-  cudaFree(pl->rhs);
-  cudaFree(pl->coarse_inv);
-  cudaFree(pl->coarse_inv_f);
-  cudaFree(pl->coarse_tmp);
-  cudaFree(pl->scal);
-  cudaFree(pl->red_part);
-  cudaFree(pl->red_count);
-  cudaFree(pl->err_flag);
-  cudaFree(pl->sort_hist);
-  cudaFree(pl->seg_tmp);
+  // every device buffer of the plan was allocated by plan_alloc
+  for (auto& kv : pl->dev_sizes) cudaFree(kv.first);
+  pl->dev_sizes.clear();
+  pl->dev_bytes = 0;
   if (pl->host_scal) cudaFreeHost(pl->host_scal);
   for (auto& gr : pl->graph)
     if (gr.exec) cudaGraphExecDestroy(gr.exec);
@@ -916,10 +920,10 @@ int sps_set_points(sps_plan* pl, int64_t n, const void* x, const void* y, int dt
   if (n > pl->n_cap || dtype != pl->dtype) {
     free_points(pl);
     int rc;
-    if ((rc = alloc((char**)&pl->x_sorted, (long long)es * P * n)) || (rc = alloc(&pl->y_sorted, n)) ||
-        (rc = alloc(&pl->keys, n)) || (rc = alloc(&pl->keys_tmp, n)) || (rc = alloc(&pl->perm, n)) ||
-        (rc = alloc(&pl->perm_tmp, n)) ||
-        (dtype == SPS_F64 && (rc = alloc(&pl->x32_sorted, (long long)P * n)))) {
+    if ((rc = palloc(pl, (char**)&pl->x_sorted, (long long)es * P * n)) || (rc = palloc(pl, &pl->y_sorted, n)) ||
+        (rc = palloc(pl, &pl->keys, n)) || (rc = palloc(pl, &pl->keys_tmp, n)) || (rc = palloc(pl, &pl->perm, n)) ||
+        (rc = palloc(pl, &pl->perm_tmp, n)) ||
+        (dtype == SPS_F64 && (rc = palloc(pl, &pl->x32_sorted, (long long)P * n)))) {
       free_points(pl);
       return rc;
     }
@@ -929,23 +933,24 @@ int sps_set_points(sps_plan* pl, int64_t n, const void* x, const void* y, int dt
   pl->n = n;
   pl->dtype = dtype;
   // device copies of host inputs
-  DevBuf hx, hy;
+  DevBuf hx(pl), hy(pl);
   const void* xd = x;
   const void* yd = y;
   if (mem == SPS_MEM_HOST) {
-    SPS_TRY(alloc((char**)&hx.p, (long long)es * P * n));
-    SPS_TRY(alloc((char**)&hy.p, (long long)es * n));
+    SPS_TRY(palloc(pl, (char**)&hx.p, (long long)es * P * n));
+    SPS_TRY(palloc(pl, (char**)&hy.p, (long long)es * n));
     SPS_CUDA(cudaMemcpyAsync(hx.p, x, es * P * n, cudaMemcpyHostToDevice, st));
     SPS_CUDA(cudaMemcpyAsync(hy.p, y, es * n, cudaMemcpyHostToDevice, st));
     xd = hx.p;
     yd = hy.p;
   }
-  SPS_TRY(compute_keys(pl, xd, dtype, st));
+  SPS_TRY(compute_keys(pl, xd, yd, dtype, st));
   int bad = 0;
   SPS_CUDA(cudaMemcpyAsync(&bad, pl->err_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
   SPS_CUDA(cudaStreamSynchronize(st));
-  if (bad) {
-    set_error("a point lies outside [lo, hi] or is not finite");
+  if (bad & ERR_DOMAIN) {
+    SPS_CUDA(cudaMemsetAsync(pl->err_flag, 0, sizeof(int), st));
+    set_error("a point lies outside [lo, hi], or a coordinate or response is not finite");
     return SPS_EDOM;
   }
   SPS_TRY(radix_sort(pl, P * pl->Lbits, st));
@@ -967,7 +972,11 @@ int sps_set_points(sps_plan* pl, int64_t n, const void* x, const void* y, int dt
   }
   SPS_TRY(read_scalars(pl, st));
   pl->rhs_norm = std::sqrt(pl->host_scal[S_TMP]);
-  SPS_TRY(coarse_assemble(pl, st));
+  if (!std::isfinite(pl->rhs_norm)) {
+    set_error("the right-hand side Phi'y is not finite");
+    return SPS_EDOM;
+  }
+  if (!pl->opt.coarse_cg) SPS_TRY(coarse_assemble(pl, st));
   SPS_TRY(assemble_coarse_levels(pl, st));
   // FP64 mode: basis values of the points on every matrix-free level (>= 2)
   if (pl->opt.precision == SPS_PREC_FP64) {
@@ -976,19 +985,17 @@ int sps_set_points(sps_plan* pl, int64_t n, const void* x, const void* y, int dt
       if (L.st_d) continue;
       const long long need = pl->n * 4LL * P;
       if (L.pre_cap < need) {
-        cudaFree(L.pre);
-        L.pre = nullptr;
+        pfree(pl, L.pre);
         L.pre_cap = 0;
-        SPS_TRY(alloc(&L.pre, need));
+        SPS_TRY(palloc(pl, &L.pre, need));
         L.pre_cap = need;
       }
       if (P == 3) {   // products for the four-lane layout
         const long long need2 = pl->n * (long long)PRE2_STRIDE;
         if (L.pre2_cap < need2) {
-          cudaFree(L.pre2);
-          L.pre2 = nullptr;
+          pfree(pl, L.pre2);
           L.pre2_cap = 0;
-          SPS_TRY(alloc(&L.pre2, need2));
+          SPS_TRY(palloc(pl, &L.pre2, need2));
           L.pre2_cap = need2;
         }
       }
@@ -1006,6 +1013,7 @@ int sps_set_points(sps_plan* pl, int64_t n, const void* x, const void* y, int dt
   pl->lev[0].omega = pl->opt.omega > 0.0 ? pl->opt.omega : 0.0;
   SPS_CUDA(cudaStreamSynchronize(st));
   SPS_CUDA(cudaGetLastError());
+  SPS_TRY(check_device_errors(pl, st));
   pl->have_points = true;
   ++pl->gen;
   return SPS_OK;
@@ -1036,6 +1044,7 @@ int sps_solve(sps_plan* pl, double* coef, int mem, double tol, sps_result* res_o
   }
   SPS_TRY(copy_out(coef, pl->x, KG, mem, st));
   SPS_CUDA(cudaStreamSynchronize(st));
+  SPS_TRY(check_device_errors(pl, st));
   res.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   if (res_out) *res_out = res;
   return res.status;
@@ -1049,8 +1058,10 @@ int sps_solve_batch(sps_plan* const* plans, int count, double* const* coefs, int
   }
   for (int i = 0; i < count; ++i) {
     SPS_TRY(check_plan_points(plans[i]));
-    if (plans[i]->P > 3 || !coefs[i] || plans[i]->lev[plans[i]->G - 1].geom.K >= (1LL << 31)) {
-      set_error("batched solves take P <= 3, fewer than 2^31 coefficients and a coefficient buffer per problem");
+    if (plans[i]->P > 3 || !coefs[i] || plans[i]->lev[plans[i]->G - 1].geom.K >= (1LL << 31) ||
+        plans[i]->opt.coarse_cg) {
+      set_error("batched solves take P <= 3, fewer than 2^31 coefficients, the dense coarse solver and a "
+                "coefficient buffer per problem");
       return SPS_EINVAL;
     }
     if (plans[i]->rhs_norm == 0.0) {
@@ -1076,17 +1087,18 @@ int sps_apply(sps_plan* pl, int level, int prec, const double* v, double* u, int
   SPS_TRY(check_level(pl, level, 1));
   cudaStream_t st = as_stream(stream);
   const long long K = pl->lev[level - 1].geom.K;
-  DevBuf bi, bo;
+  DevBuf bi(pl), bo(pl);
   const double* vd;
   double* ud;
   SPS_TRY(stage_in(v, K, mem, bi, &vd, st));
   SPS_TRY(stage_out_ptr(u, K, mem, bo, &ud));
   if (prec == SPS_PREC_MIXED) {
-    SPS_TRY(run_f32(K, K, vd, ud, [&](const float* a, float* b) { return apply_level<float>(pl, level, a, b, st); },
+    SPS_TRY(run_f32(pl, K, K, vd, ud, [&](const float* a, float* b) { return apply_level<float>(pl, level, a, b, st); },
                     st));
   } else {
     SPS_TRY(apply_level<double>(pl, level, vd, ud, st));
   }
+  SPS_TRY(check_device_errors(pl, st));
   return finish_out(u, ud, K, mem, st);
 }
 
@@ -1095,13 +1107,13 @@ int sps_point_apply(sps_plan* pl, int level, int prec, const double* v, double* 
   SPS_TRY(check_level(pl, level, 1));
   cudaStream_t st = as_stream(stream);
   const long long K = pl->lev[level - 1].geom.K;
-  DevBuf bi, bo;
+  DevBuf bi(pl), bo(pl);
   const double* vd;
   double* ud;
   SPS_TRY(stage_in(v, K, mem, bi, &vd, st));
   SPS_TRY(stage_out_ptr(u, K, mem, bo, &ud));
   if (prec == SPS_PREC_MIXED) {
-    SPS_TRY(run_f32(K, K, vd, ud,
+    SPS_TRY(run_f32(pl, K, K, vd, ud,
                     [&](const float* a, float* b) {
                       SPS_CUDA(cudaMemsetAsync(b, 0, sizeof(float) * K, st));
                       return point_op<float>(pl, level, PT_APPLY, a, b, st);
@@ -1111,6 +1123,7 @@ int sps_point_apply(sps_plan* pl, int level, int prec, const double* v, double* 
     SPS_CUDA(cudaMemsetAsync(ud, 0, sizeof(double) * K, st));
     SPS_TRY(point_op<double>(pl, level, PT_APPLY, vd, ud, st));
   }
+  SPS_TRY(check_device_errors(pl, st));
   return finish_out(u, ud, K, mem, st);
 }
 
@@ -1141,13 +1154,13 @@ int sps_penalty_apply(sps_plan* pl, int level, int prec, const double* v, double
   SPS_TRY(check_level(pl, level, 1));
   cudaStream_t st = as_stream(stream);
   const long long K = pl->lev[level - 1].geom.K;
-  DevBuf bi, bo;
+  DevBuf bi(pl), bo(pl);
   const double* vd;
   double* ud;
   SPS_TRY(stage_in(v, K, mem, bi, &vd, st));
   SPS_TRY(stage_out_ptr(u, K, mem, bo, &ud));
   if (prec == SPS_PREC_MIXED) {
-    SPS_TRY(run_f32(K, K, vd, ud,
+    SPS_TRY(run_f32(pl, K, K, vd, ud,
                     [&](const float* a, float* b) { return penalty_apply<float>(pl, level, a, b, 1.0, st); }, st));
   } else {
     SPS_TRY(penalty_apply<double>(pl, level, vd, ud, 1.0, st));
@@ -1172,13 +1185,13 @@ int sps_prolong(sps_plan* pl, int level, int prec, const double* c, double* f, i
   SPS_TRY(check_level(pl, level, 2));
   cudaStream_t st = as_stream(stream);
   const long long Kc = pl->lev[level - 2].geom.K, Kf = pl->lev[level - 1].geom.K;
-  DevBuf bi, bo;
+  DevBuf bi(pl), bo(pl);
   const double* cd;
   double* fd;
   SPS_TRY(stage_in(c, Kc, mem, bi, &cd, st));
   SPS_TRY(stage_out_ptr(f, Kf, mem, bo, &fd));
   if (prec == SPS_PREC_MIXED) {
-    SPS_TRY(run_f32(Kc, Kf, cd, fd, [&](const float* a, float* b) { return prolong_sub<float>(pl, level, a, b, 0, st); },
+    SPS_TRY(run_f32(pl, Kc, Kf, cd, fd, [&](const float* a, float* b) { return prolong_sub<float>(pl, level, a, b, 0, st); },
                     st));
   } else {
     SPS_TRY(prolong_sub<double>(pl, level, cd, fd, 0, st));
@@ -1191,13 +1204,13 @@ int sps_restrict(sps_plan* pl, int level, int prec, const double* f, double* c, 
   SPS_TRY(check_level(pl, level, 2));
   cudaStream_t st = as_stream(stream);
   const long long Kc = pl->lev[level - 2].geom.K, Kf = pl->lev[level - 1].geom.K;
-  DevBuf bi, bo;
+  DevBuf bi(pl), bo(pl);
   const double* fd;
   double* cd;
   SPS_TRY(stage_in(f, Kf, mem, bi, &fd, st));
   SPS_TRY(stage_out_ptr(c, Kc, mem, bo, &cd));
   if (prec == SPS_PREC_MIXED) {
-    SPS_TRY(run_f32(Kf, Kc, fd, cd,
+    SPS_TRY(run_f32(pl, Kf, Kc, fd, cd,
                     [&](const float* a, float* b) { return restrict_res<float>(pl, level, a, nullptr, b, st); }, st));
   } else {
     SPS_TRY(restrict_res<double>(pl, level, fd, nullptr, cd, st));
@@ -1209,12 +1222,18 @@ int sps_coarse_solve(sps_plan* pl, const double* r, double* e, int mem, void* st
   SPS_TRY(check_plan_points(pl));
   cudaStream_t st = as_stream(stream);
   const long long K = pl->lev[0].geom.K;
-  DevBuf bi, bo;
+  DevBuf bi(pl), bo(pl);
   const double* rd;
   double* ed;
   SPS_TRY(stage_in(r, K, mem, bi, &rd, st));
   SPS_TRY(stage_out_ptr(e, K, mem, bo, &ed));
-  SPS_TRY(coarse_solve<double>(pl, rd, ed, st));
+  if (pl->opt.coarse_cg) {   // level-1 vectors other than the penalty temporaries
+    SPS_CUDA(cudaMemcpyAsync(pl->lev[0].d.b, rd, sizeof(double) * K, cudaMemcpyDeviceToDevice, st));
+    SPS_TRY(coarse_cg<double>(pl, pl->lev[0].d.b, ed, pl->dtmp[6], pl->dtmp[7], st));
+    SPS_TRY(check_device_errors(pl, st));
+  } else {
+    SPS_TRY(coarse_solve<double>(pl, rd, ed, st));
+  }
   return finish_out(e, ed, K, mem, st);
 }
 
@@ -1223,7 +1242,7 @@ int sps_vcycle(sps_plan* pl, int prec, const double* r, double* z, int mem, void
   cudaStream_t st = as_stream(stream);
   const int G = pl->G;
   const long long K = pl->lev[G - 1].geom.K;
-  DevBuf bi, bo;
+  DevBuf bi(pl), bo(pl);
   const double* rd;
   double* zd;
   SPS_TRY(stage_in(r, K, mem, bi, &rd, st));
@@ -1238,6 +1257,7 @@ int sps_vcycle(sps_plan* pl, int prec, const double* r, double* z, int mem, void
     SPS_TRY(vcycle_into<double>(pl, pl->r, zd, st));
   }
   SPS_CUDA(cudaStreamSynchronize(st));
+  SPS_TRY(check_device_errors(pl, st));
   return finish_out(z, zd, K, mem, st);
 }
 
@@ -1270,6 +1290,40 @@ int sps_get_tuning(const sps_plan* pl, int level, int* tile, int* lanes_r) {
   if (tile) *tile = pl->lev[level - 1].geom.ts;
   if (lanes_r) *lanes_r = pl->lev[level - 1].lanes_r;
   return SPS_OK;
+}
+
+int sps_plan_device_bytes(const sps_plan* pl, int64_t* bytes) {
+  if (!pl || !bytes) {
+    set_error("null argument");
+    return SPS_EINVAL;
+  }
+  *bytes = pl->dev_bytes;
+  return SPS_OK;
+}
+
+int sps_level_matrix(sps_plan* pl, int level, double* out, int64_t* entries, int mem, void* stream) {
+  SPS_TRY(check_plan_points(pl));
+  SPS_TRY(check_level(pl, level, 1));
+  if (!entries || (mem != SPS_MEM_HOST && mem != SPS_MEM_DEVICE)) {
+    set_error("invalid entries pointer or mem");
+    return SPS_EINVAL;
+  }
+  cudaStream_t st = as_stream(stream);
+  const Level& L = pl->lev[level - 1];
+  const long long K = L.geom.K;
+  long long count = 0;
+  if (level == 1 && pl->coarse_A) count = K * K;
+  else if (L.st_d || L.st_f) count = (long long)L.S * K;
+  *entries = count;
+  if (!out || count == 0) return SPS_OK;
+  if (level == 1 && pl->coarse_A) return copy_out(out, pl->coarse_A, count, mem, st);
+  if (L.st_d) return copy_out(out, L.st_d, count, mem, st);
+  DevBuf bo(pl);   // mixed plans hold the FP32 stencil only: widen it
+  double* od;
+  SPS_TRY(stage_out_ptr(out, count, mem, bo, &od));
+  SPS_TRY(vec_cast_f2d(od, L.st_f, count, st));
+  SPS_CUDA(cudaStreamSynchronize(st));
+  return finish_out(out, od, count, mem, st);
 }
 
 int sps_get_omega(const sps_plan* pl, double* omega) {
@@ -1305,8 +1359,11 @@ int sps_probe_fma_rate(int fp, double* fma_per_s, void* stream) {
   int dev = 0, sms = 0;
   SPS_CUDA(cudaGetDevice(&dev));
   SPS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  DevBuf out;
-  SPS_TRY(alloc((double**)&out.p, 1));
+  struct Out {
+    void* p = nullptr;
+    ~Out() { if (p) cudaFree(p); }
+  } out;
+  SPS_CUDA(cudaMalloc(&out.p, sizeof(double)));
   const int threads = 256, blocks = sms * 8;
   const int iters = fp ? 4000 : 100000;
   cudaEvent_t e0, e1;

@@ -53,7 +53,8 @@ struct BatchProblem {
   double *x, *r, *z, *p, *v, *rprev;
   float* p32;
   const double* rhs;
-  const double* coarse_inv;
+  const double* coarse_z;    // A_1^-1 = Z'Z: Z and Z' (K_1 x K_1 each)
+  const double* coarse_zt;
   BatchLevel lev[MAXL];
 };
 
@@ -396,12 +397,20 @@ __device__ void cta_vcycle(const BatchProblem& pb, const float* bG, float* xG, c
     cta_restrict(pb, g, L.u, b, B(g - 1), tm);
   }
   {
+    // e = Z'(Z b) through the coarse level's spare vector u
     const long long K1 = pb.lev[0].geom.K;
     const float* b1 = B(1);
     float* x1 = X(1);
+    float* y1 = pb.lev[0].u;
     for (long long row = tm.start(); row < K1; row += tm.stride()) {
       double s = 0.0;
-      for (long long c = 0; c < K1; ++c) s = fma(pb.coarse_inv[row * K1 + c], (double)b1[c], s);
+      for (long long c = 0; c < K1; ++c) s = fma(pb.coarse_z[row * K1 + c], (double)b1[c], s);
+      y1[row] = (float)s;
+    }
+    team_sync(tm);
+    for (long long row = tm.start(); row < K1; row += tm.stride()) {
+      double s = 0.0;
+      for (long long c = 0; c < K1; ++c) s = fma(pb.coarse_zt[row * K1 + c], (double)y1[c], s);
       x1[row] = (float)s;
     }
     team_sync(tm);
@@ -611,7 +620,8 @@ int solve_batch(sps_plan* const* plans, int count, double* const* coefs, int mem
     b.rprev = pl->rprev;
     b.p32 = pl->p32;
     b.rhs = pl->rhs;
-    b.coarse_inv = pl->coarse_inv;
+    b.coarse_z = pl->coarse_inv;
+    b.coarse_zt = pl->coarse_invt;
     for (int g = 0; g < pl->G; ++g) {
       const Level& L = pl->lev[g];
       BatchLevel& bl = b.lev[g];

@@ -375,50 +375,89 @@ __global__ void __launch_bounds__(32 * SPMV_Y) k_stencil_spmv(const T* __restric
   }
 }
 
-// In-place Gauss-Jordan inversion of the SPD coarse matrix, one pivot per
-// launch.  rowk/colk hold row and column k as they were before step k; the
-// threads that write row/column k+1 also record them for the next step.
-__global__ void k_gj_init(const double* __restrict__ A, long long K, double* __restrict__ rowk,
-                          double* __restrict__ colk) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < K; i += (long long)gridDim.x * blockDim.x) {
-    rowk[i] = A[i];
-    colk[i] = A[i * K];
+// Inverse Cholesky factor of the SPD coarse matrix: Z = L^-1 with A = L L'.
+// Step k of the Cholesky elimination is applied to [A | I]: the trailing part
+// of A (lower triangle) is updated, a_ij -= a_ik a_jk / a_kk, and the same row
+// operations, row_i -= (a_ik / a_kk) row_k, turn I into L^-1; row k is scaled
+// by 1 / sqrt(a_kk) one launch later (when nothing reads it any more).  The
+// coarse solve is then e = Z' (Z r): Z'Z is symmetric positive definite for
+// any nonsingular Z, so the coarse correction keeps the V-cycle an SPD
+// preconditioner however ill-conditioned A_1 is, and Z's rounding errors grow
+// like sqrt(cond(A_1)) instead of cond(A_1) for an explicit inverse.
+// Launch k covers rows k-1 .. K-1 (launch K only scales row K-1).
+__global__ void k_chol_inv_step(double* __restrict__ A, double* __restrict__ Z, double* __restrict__ piv, long long K,
+                                int k) {
+  const long long r0 = k > 0 ? k - 1 : 0;
+  const double p = k < K ? A[(long long)k * K + k] : 1.0;
+  const double ip = 1.0 / p;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (K - r0) * K;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long i = r0 + e / K, j = e - (e / K) * K;
+    if (i == k - 1) {
+      if (j <= i) Z[i * K + j] /= sqrt(piv[i]);
+    } else if (i == k) {
+      if (j == 0) piv[k] = p;
+    } else {
+      const double l = A[i * K + k] * ip;
+      if (j > k && j <= i) A[i * K + j] -= l * A[j * K + k];
+      else if (j <= k) Z[i * K + j] -= l * Z[(long long)k * K + j];
+    }
   }
 }
 
-__global__ void k_gj_step(double* __restrict__ A, long long K, int k, const double* __restrict__ rowk,
-                          const double* __restrict__ colk, double* __restrict__ rown, double* __restrict__ coln) {
-  const double piv = rowk[k];
-  const double ipiv = 1.0 / piv;
+__global__ void k_identity(double* __restrict__ Z, long long K) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < K * K;
+       e += (long long)gridDim.x * blockDim.x)
+    Z[e] = (e / K == e - (e / K) * K) ? 1.0 : 0.0;
+}
+
+// Z <- Z S (columns scaled: (S A S)^-1 = Z_s' Z_s gives A^-1 = (Z_s S)' (Z_s S)), and Zt = Z'.
+__global__ void k_unscale_transpose(double* __restrict__ Z, double* __restrict__ Zt, const double* __restrict__ sc,
+                                    long long K) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < K * K;
        e += (long long)gridDim.x * blockDim.x) {
-    const long long i = e / K, j = e % K;
-    double a;
-    if (i == k && j == k) a = ipiv;
-    else if (i == k) a = rowk[j] * ipiv;
-    else if (j == k) a = -colk[i] * ipiv;
-    else a = A[e] - colk[i] * rowk[j] * ipiv;
-    A[e] = a;
-    if (i == k + 1) rown[j] = a;
-    if (j == k + 1) coln[i] = a;
+    const long long i = e / K, j = e - (e / K) * K;
+    const double z = Z[e] * sc[j];
+    Z[e] = z;
+    Zt[j * K + i] = z;
   }
 }
 
-__global__ void k_f64_to_f32(const double* __restrict__ a, float* __restrict__ b, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    b[i] = (float)a[i];
+// Symmetric Jacobi scaling of the coarse matrix: s_i = 1 / sqrt(A_ii), and
+// out = S A S.  The inverse is formed from the scaled matrix (unit diagonal;
+// for the workloads' A_1 its condition number is 4-6 orders of magnitude
+// below that of A_1) and scaled back, A^-1 = S (S A S)^-1 S.
+__global__ void k_coarse_scale(const double* __restrict__ A, long long K, double* __restrict__ sc) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < K; i += (long long)gridDim.x * blockDim.x) {
+    const double d = A[i * K + i];
+    sc[i] = d > 0.0 ? 1.0 / sqrt(d) : 1.0;
+  }
 }
 
-// e = A_1^{-1} r, one warp per row, FP64 arithmetic.
+// (in place when out == A: each entry is read and written by the same thread)
+__global__ void k_scale_sym(const double* A, long long K, const double* __restrict__ sc, double* out) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < K * K;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e / K, j = e - (e / K) * K;
+    out[e] = sc[i] * A[e] * sc[j];
+  }
+}
+
+// One warp per row, FP64 arithmetic: mode 0: y = M x; 1: y = b - M x; 2: y += M x.
 template <typename T>
-__global__ void k_gemv(const double* __restrict__ Ainv, long long K, const T* __restrict__ r, T* __restrict__ e) {
+__global__ void k_gemv(const double* __restrict__ M, long long K, const T* __restrict__ x, T* __restrict__ y,
+                       const T* __restrict__ b, int mode) {
   const int lane = threadIdx.x & 31;
   for (long long row = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; row < K;
        row += ((long long)gridDim.x * blockDim.x) >> 5) {
     double s = 0.0;
-    for (long long c = lane; c < K; c += 32) s = fma(Ainv[row * K + c], (double)r[c], s);
+    for (long long c = lane; c < K; c += 32) s = fma(M[row * K + c], (double)x[c], s);
     for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) e[row] = T(s);
+    if (lane == 0) {
+      if (mode == 0) y[row] = T(s);
+      else if (mode == 1) y[row] = T((double)b[row] - s);
+      else y[row] = T((double)y[row] + s);
+    }
   }
 }
 
@@ -565,6 +604,76 @@ __global__ void k_residual(double* __restrict__ r, const double* __restrict__ b,
   finish_reduction<1>(vals, part, count, out, sh);
 }
 
+// ---- inner Jacobi-preconditioned CG on the coarse level (Section 3.2, coarse
+// grid solver: a matrix-free CG instead of a factorisation).  Vectors in T,
+// reductions and scalars in FP64; scalar slots in plan->scal:
+constexpr int C_PQ = 16, C_RZ0 = 18, C_RZ1 = 20;
+
+// e = 0; r = b; p = D^-1 b; scal[C_RZ0] = b' D^-1 b
+template <typename T>
+__global__ void k_ccg_init(const T* __restrict__ b, const T* __restrict__ dinv, T* __restrict__ e,
+                           T* __restrict__ r, T* __restrict__ p, long long n, double* scal, double* part,
+                           unsigned int* count) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const T bi = b[i];
+    const T zi = dinv[i] * bi;
+    e[i] = T(0);
+    r[i] = bi;
+    p[i] = zi;
+    s = fma((double)bi, (double)zi, s);
+  }
+  double v[1];
+  v[0] = block_sum(s, sh);
+  finish_reduction<1>(v, part, count, scal + C_RZ0, sh);
+}
+
+// scal[C_PQ] = p'q
+template <typename T>
+__global__ void k_ccg_pq(const T* __restrict__ p, const T* __restrict__ q, long long n, double* scal, double* part,
+                         unsigned int* count) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    s = fma((double)p[i], (double)q[i], s);
+  double v[1];
+  v[0] = block_sum(s, sh);
+  finish_reduction<1>(v, part, count, scal + C_PQ, sh);
+}
+
+// a = rz / p'q (0 once the iteration has converged or broken down);
+// e += a p; r -= a q; scal[rz_new] = r' D^-1 r
+template <typename T>
+__global__ void k_ccg_update(T* __restrict__ e, T* __restrict__ r, const T* __restrict__ p, const T* __restrict__ q,
+                             const T* __restrict__ dinv, long long n, double* scal, int rz_old, int rz_new,
+                             double* part, unsigned int* count) {
+  __shared__ double sh[32];
+  const double pq = scal[C_PQ], rz = scal[rz_old];
+  double a = rz / pq;
+  if (!(pq > 0.0) || !isfinite(a)) a = 0.0;
+  double s = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    e[i] = T(fma(a, (double)p[i], (double)e[i]));
+    const T ri = T(fma(-a, (double)q[i], (double)r[i]));
+    r[i] = ri;
+    s = fma((double)ri, (double)(dinv[i] * ri), s);
+  }
+  double v[1];
+  v[0] = block_sum(s, sh);
+  finish_reduction<1>(v, part, count, scal + rz_new, sh);
+}
+
+// p = D^-1 r + beta p, beta = rz_new / rz_old (0 once converged)
+template <typename T>
+__global__ void k_ccg_dir(T* __restrict__ p, const T* __restrict__ r, const T* __restrict__ dinv, long long n,
+                          const double* scal, int rz_old, int rz_new) {
+  double beta = scal[rz_new] / scal[rz_old];
+  if (!(scal[rz_old] > 0.0) || !isfinite(beta)) beta = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    p[i] = T(fma(beta, (double)p[i], (double)(dinv[i] * r[i])));
+}
+
 template <typename T>
 T* tmp_of(sps_plan* pl, int i);
 template <>
@@ -700,11 +809,12 @@ int phi_assembly_launch(sps_plan* pl, const Level& L, double* out, cudaStream_t 
   return SPS_OK;
 }
 
-// Phi_g'Phi_g assembled into `out` (dense K x K, or stencil form), FP32
-// products (with FP64 accumulation) in the mixed mode and for P >= 4.
+// Phi_g'Phi_g assembled into `out` (dense K x K, or stencil form): FP64
+// basis values and products in FP64 plans; FP32 products with FP64
+// accumulation in mixed plans, whose V-cycle runs in FP32.
 template <int P>
 int coarse_phi_launch(sps_plan* pl, const Level& L, double* out, bool stencil, cudaStream_t st) {
-  const bool fp32 = pl->opt.precision == SPS_PREC_MIXED || P >= 4;
+  const bool fp32 = pl->opt.precision == SPS_PREC_MIXED;
   if (fp32) return stencil ? phi_assembly_launch<P, float, true>(pl, L, out, st)
                            : phi_assembly_launch<P, float, false>(pl, L, out, st);
   return stencil ? phi_assembly_launch<P, double, true>(pl, L, out, st)
@@ -723,32 +833,34 @@ int phi_assembly(sps_plan* pl, const Level& L, double* out, bool stencil, cudaSt
   return SPS_EINVAL;
 }
 
-// Assemble A_1 into coarse_inv and invert it in place.
+// Assemble A_1 into coarse_A; the inverse Cholesky factor of its Jacobi-scaled
+// form, scaled back, into coarse_inv (Z) and its transpose into coarse_invt.
 int coarse_assemble(sps_plan* pl, cudaStream_t st) {
   Level& L = pl->lev[0];
   const long long K = L.geom.K;
-  SPS_CUDA(cudaMemsetAsync(pl->coarse_inv, 0, sizeof(double) * K * K, st));
-  int e = phi_assembly(pl, L, pl->coarse_inv, false, st);
+  SPS_CUDA(cudaMemsetAsync(pl->coarse_A, 0, sizeof(double) * K * K, st));
+  int e = phi_assembly(pl, L, pl->coarse_A, false, st);
   if (e) return e;
   k_coarse_penalty<<<grid_blocks(K * K, EW_THREADS), EW_THREADS, 0, st>>>(L.geom, L.d.band, pl->lam,
-                                                                          pl->coarse_inv);
+                                                                          pl->coarse_A);
   SPS_CHECK_LAUNCH("coarse penalty");
-  double* rowk = pl->coarse_tmp;
-  double* colk = rowk + K;
-  double* rown = colk + K;
-  double* coln = rown + K;
-  k_gj_init<<<grid_blocks(K, EW_THREADS), EW_THREADS, 0, st>>>(pl->coarse_inv, K, rowk, colk);
-  SPS_CHECK_LAUNCH("gj init");
+  double* sc = pl->coarse_tmp;          // Jacobi scale
+  double* piv = sc + K;                  // pivots of the elimination
+  double* As = pl->coarse_tmp + 6 * K;   // scaled working copy of A_1 (K x K)
   const int blocks = grid_blocks(K * K, EW_THREADS);
-  for (int k = 0; k < K; ++k) {
-    k_gj_step<<<blocks, EW_THREADS, 0, st>>>(pl->coarse_inv, K, k, rowk, colk, rown, coln);
-    std::swap(rowk, rown);
-    std::swap(colk, coln);
+  k_coarse_scale<<<grid_blocks(K, EW_THREADS), EW_THREADS, 0, st>>>(pl->coarse_A, K, sc);
+  SPS_CHECK_LAUNCH("coarse scale");
+  k_scale_sym<<<blocks, EW_THREADS, 0, st>>>(pl->coarse_A, K, sc, As);
+  SPS_CHECK_LAUNCH("coarse scale");
+  k_identity<<<blocks, EW_THREADS, 0, st>>>(pl->coarse_inv, K);
+  SPS_CHECK_LAUNCH("coarse identity");
+  for (int k = 0; k <= K; ++k) {
+    k_chol_inv_step<<<blocks, EW_THREADS, 0, st>>>(As, pl->coarse_inv, piv, K, k);
   }
-  count_launches(K - 1);
-  SPS_CHECK_LAUNCH("gj step");
-  k_f64_to_f32<<<grid_blocks(K * K, EW_THREADS), EW_THREADS, 0, st>>>(pl->coarse_inv, pl->coarse_inv_f, K * K);
-  SPS_CHECK_LAUNCH("coarse cast");
+  count_launches(K);
+  SPS_CHECK_LAUNCH("coarse elimination");
+  k_unscale_transpose<<<blocks, EW_THREADS, 0, st>>>(pl->coarse_inv, pl->coarse_invt, sc, K);
+  SPS_CHECK_LAUNCH("coarse unscale");
   return SPS_OK;
 }
 
@@ -804,14 +916,52 @@ int stencil_apply(sps_plan* pl, int g, const T* v, T* u, cudaStream_t st) {
 template int stencil_apply<double>(sps_plan*, int, const double*, double*, cudaStream_t);
 template int stencil_apply<float>(sps_plan*, int, const float*, float*, cudaStream_t);
 
+// e = A_1^-1 r as e = Z'(Z r); in FP64 one step of iterative refinement
+// follows: e += Z'Z (r - A_1 e), with the residual from the assembled A_1
+// (the refined operator 2M - MAM, M = Z'Z, is symmetric positive definite).
 template <typename T>
 int coarse_solve(sps_plan* pl, const T* r, T* e, cudaStream_t st) {
   const long long K = pl->lev[0].geom.K;
   const int blocks = (int)std::min<long long>((K * 32 + EW_THREADS - 1) / EW_THREADS, 152LL * 16);
-  k_gemv<T><<<blocks, EW_THREADS, 0, st>>>(pl->coarse_inv, K, r, e);
+  T* y = (T*)(pl->coarse_tmp + 2 * K);
+  k_gemv<T><<<blocks, EW_THREADS, 0, st>>>(pl->coarse_inv, K, r, y, nullptr, 0);
+  k_gemv<T><<<blocks, EW_THREADS, 0, st>>>(pl->coarse_invt, K, y, e, nullptr, 0);
+  count_launches(1);
   SPS_CHECK_LAUNCH("coarse solve");
+  if constexpr (sizeof(T) == 8) {
+    T* res = (T*)(pl->coarse_tmp + 3 * K);
+    k_gemv<T><<<blocks, EW_THREADS, 0, st>>>(pl->coarse_A, K, e, res, r, 1);
+    k_gemv<T><<<blocks, EW_THREADS, 0, st>>>(pl->coarse_inv, K, res, y, nullptr, 0);
+    k_gemv<T><<<blocks, EW_THREADS, 0, st>>>(pl->coarse_invt, K, y, e, nullptr, 2);
+    count_launches(2);
+    SPS_CHECK_LAUNCH("coarse refinement");
+  }
   return SPS_OK;
 }
+
+template <typename T>
+int coarse_cg(sps_plan* pl, const T* b, T* e, T* r1, T* p1, cudaStream_t st) {
+  Level& L = pl->lev[0];
+  LevelVecs<T>& V = vecs<T>(L);
+  const long long K = L.geom.K;
+  T* q = V.u;
+  k_ccg_init<T><<<RED_BLOCKS, EW_THREADS, 0, st>>>(b, V.dinv, e, r1, p1, K, pl->scal, pl->red_part, pl->red_count);
+  SPS_CHECK_LAUNCH("coarse CG init");
+  int rz_old = C_RZ0, rz_new = C_RZ1;
+  for (int it = 0; it < pl->opt.coarse_iters; ++it) {
+    SPS_TRY(apply_level<T>(pl, 1, p1, q, st));
+    k_ccg_pq<T><<<RED_BLOCKS, EW_THREADS, 0, st>>>(p1, q, K, pl->scal, pl->red_part, pl->red_count);
+    k_ccg_update<T><<<RED_BLOCKS, EW_THREADS, 0, st>>>(e, r1, p1, q, V.dinv, K, pl->scal, rz_old, rz_new,
+                                                       pl->red_part, pl->red_count);
+    k_ccg_dir<T><<<grid_blocks(K, EW_THREADS), EW_THREADS, 0, st>>>(p1, r1, V.dinv, K, pl->scal, rz_old, rz_new);
+    count_launches(2);
+    SPS_CHECK_LAUNCH("coarse CG step");
+    std::swap(rz_old, rz_new);
+  }
+  return SPS_OK;
+}
+template int coarse_cg<double>(sps_plan*, const double*, double*, double*, double*, cudaStream_t);
+template int coarse_cg<float>(sps_plan*, const float*, float*, float*, float*, cudaStream_t);
 template int coarse_solve<double>(sps_plan*, const double*, double*, cudaStream_t);
 template int coarse_solve<float>(sps_plan*, const float*, float*, cudaStream_t);
 

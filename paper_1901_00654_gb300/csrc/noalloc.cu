@@ -9,15 +9,22 @@
 // directly and keeps its temporaries in a fixed device array instead.
 //
 // The scratch is one file-scope __device__ array of SPS_NOALLOC_MAX_COEF
-// coefficients times 6 doubles (12 MiB), present on every GPU that loads
-// the library until the process exits.  Every call shares it, so calls that
-// overlap on the GPU (different streams, different host threads) race on it.
-// Each sweep writes all K entries of its outputs before the next sweep reads
-// them, so nothing in the scratch has to start at zero.
+// coefficients times 6 doubles (12 MiB).  It belongs to this file's module:
+// with CUDA's default lazy module loading the module -- and so the 12 MiB --
+// is loaded on a device at the first call there (the cudaGetSymbolAddress
+// of the set-up), and stays until the process exits; with
+// CUDA_MODULE_LOADING=EAGER it is loaded with the library.  A caller whose
+// memory is about to be handed to another allocator should therefore make
+// one call first.  Every call shares the array, so calls that overlap on the
+// GPU (different streams, different host threads) race on it.  Each sweep
+// writes all K entries of its outputs before the next sweep reads them, so
+// nothing in the scratch has to start at zero.
 //
 // The first call on a device does the set-up (cudaGetSymbolAddress of the
 // scratch, upload of the cubic element matrices to constant memory); make
-// that first call before any stream capture.
+// that first call before any stream capture.  The cached set-up is not
+// redone after cudaDeviceReset: the entry point must not be used on a device
+// after a reset in the same process.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -173,6 +180,17 @@ extern "C" int sps_penalty_apply_noalloc(int P, const int* intervals, const doub
   if (g.K > NOALLOC_MAX) {
     set_error("grid has more than SPS_NOALLOC_MAX_COEF (262144) coefficients; use sps_penalty_apply with a plan");
     return SPS_EINVAL;
+  }
+  // u is written while v is still read (for P = 1 the single sweep reads v[k +- 3]
+  // while writing u[k]): the two must not overlap
+  {
+    const char* vb = (const char*)v;
+    const char* ub = (const char*)u;
+    const size_t bytes = sizeof(double) * (size_t)g.K;
+    if (ub < vb + bytes && vb < ub + bytes) {
+      set_error("u and v must not overlap");
+      return SPS_EINVAL;
+    }
   }
   int dev = 0;
   SPS_CUDA(cudaGetDevice(&dev));

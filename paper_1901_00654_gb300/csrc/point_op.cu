@@ -27,6 +27,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "sps_internal.h"
 
@@ -66,7 +67,7 @@ k_point(const WorkItem* __restrict__ items, const int* __restrict__ run_begin,
         const unsigned long long* __restrict__ run_cell, const int* __restrict__ run_order,
         const CT* __restrict__ xs, long long n,
         const double* __restrict__ ys, const T* __restrict__ v, T* __restrict__ u, LevelGeom geom,
-        const double* __restrict__ pre = nullptr) {
+        int* __restrict__ err, const double* __restrict__ pre = nullptr) {
   constexpr int R = RR > 0 ? RR : (P < 3 ? P : 3);   // dimensions held in a lane's registers
   constexpr int NR = ipow4(R);
   constexpr int F = P - R;                    // leading dimensions fixed per lane
@@ -101,10 +102,15 @@ k_point(const WorkItem* __restrict__ items, const int* __restrict__ run_begin,
     s_cell[e] = cl;
   }
   if (!PRE) {
-    // the host sizes the shared memory by the largest item; never stage past it
+    // The host sizes the shared memory by the largest item.  Never stage past
+    // it: if an item ever exceeded it, its contribution is skipped and the
+    // error flag makes the calling sps_* return SPS_EINTERNAL.
     unsigned dsm;
     asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dsm));
-    if (xoff + (size_t)P * npts * sizeof(CT) > dsm) return;
+    if (xoff + (size_t)P * npts * sizeof(CT) > dsm) {
+      if (threadIdx.x == 0) atomicOr(err, ERR_SMEM);
+      return;
+    }
 #pragma unroll
     for (int p = 0; p < P; ++p)
       for (int e = threadIdx.x; e < npts; e += blockDim.x) xsh[p * npts + e] = xs[(long long)p * n + pbeg + e];
@@ -431,6 +437,29 @@ struct ProfileState {
 ProfileState g_prof;
 constexpr int PROFILE_MAX = 8192;
 
+// cudaFuncSetAttribute applies to the current device only: each kernel
+// instantiation records the devices (bit per ordinal) it was raised on.
+template <typename Kern>
+int raise_smem(Kern kern, std::atomic<unsigned long long>& done) {
+  int dev = 0;
+  SPS_CUDA(cudaGetDevice(&dev));
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (!(done.load(std::memory_order_acquire) & bit)) {
+    SPS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)POINT_SMEM_MAX));
+    done.fetch_or(bit, std::memory_order_release);
+  }
+  return SPS_OK;
+}
+
+template <typename Kern, typename... Args>
+int launch_k(Kern kern, std::atomic<unsigned long long>& attr, int grid, size_t smem, cudaStream_t st,
+             Args... args) {
+  SPS_TRY(raise_smem(kern, attr));
+  kern<<<grid, POINT_THREADS, smem, st>>>(args...);
+  SPS_CHECK_LAUNCH("point operator");
+  return SPS_OK;
+}
+
 template <int P, typename T, typename CT, int MODE>
 int launch_point(sps_plan* pl, const Level& L, const T* v, T* u, cudaStream_t st) {
   if (L.nitems == 0) return SPS_OK;
@@ -441,86 +470,68 @@ int launch_point(sps_plan* pl, const Level& L, const T* v, T* u, cudaStream_t st
     set_error("tile too large for the point operator's shared memory");
     return SPS_EINVAL;
   }
-  static bool attr_set = false;
-  if (!attr_set) {
-    SPS_CUDA(cudaFuncSetAttribute(k_point<P, T, CT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)POINT_SMEM_MAX));
-    attr_set = true;
-  }
   const bool timed = MODE == PT_APPLY && g_prof.active && g_prof.used < PROFILE_MAX;
   if (timed) SPS_CUDA(record_event(g_prof.ev[2 * g_prof.used], st));
   const CT* xs = sizeof(CT) == 4 ? (const CT*)pl->x32_sorted : (const CT*)pl->x_sorted;
+  int rc = SPS_OK;
+  bool done = false;
   if constexpr (sizeof(T) == 8 && MODE == PT_APPLY) {
     if (L.pre) {
-      static bool attr_pre = false;
-      if (!attr_pre) {
-        SPS_CUDA(cudaFuncSetAttribute(k_point<P, T, CT, MODE, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)POINT_SMEM_MAX));
-        attr_pre = true;
-      }
       const size_t smem_pre = (size_t)2 * L.geom.patch * sizeof(T) + 16;
       // P = 3, 4: the 4^(P-2)-lane layout (16 sums per lane) when chosen: about
       // 10 % more FP64 operations per point, but four times the resident warps
       // and runs of more similar length within a warp
       if constexpr (P == 3) {
         if (L.lanes_r == 2 && L.pre2) {   // products of the last two dimensions precomputed
-          static bool attr_pre22 = false;
-          if (!attr_pre22) {
-            SPS_CUDA(cudaFuncSetAttribute(k_point<P, T, CT, MODE, 2, 2>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)POINT_SMEM_MAX));
-            attr_pre22 = true;
-          }
-          k_point<P, T, CT, MODE, 2, 2><<<L.nitems, POINT_THREADS, smem_pre, st>>>(
-              L.items, L.run_begin, L.run_cell, L.run_order, xs, pl->n, pl->y_sorted, v, u, L.geom, L.pre2);
-          SPS_CHECK_LAUNCH("point operator");
-          if (timed) SPS_CUDA(record_event(g_prof.ev[2 * g_prof.used++ + 1], st));
-          return SPS_OK;
+          static std::atomic<unsigned long long> a22{0};
+          rc = launch_k(k_point<P, T, CT, MODE, 2, 2>, a22, L.nitems, smem_pre, st, L.items, L.run_begin, L.run_cell,
+                        L.run_order, xs, pl->n, (const double*)pl->y_sorted, v, u, L.geom, pl->err_flag,
+                        (const double*)L.pre2);
+          done = true;
         }
       }
       if constexpr (P == 3 || P == 4) {
-        if (L.lanes_r == 2) {
-          static bool attr_pre2 = false;
-          if (!attr_pre2) {
-            SPS_CUDA(cudaFuncSetAttribute(k_point<P, T, CT, MODE, 1, 2>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)POINT_SMEM_MAX));
-            attr_pre2 = true;
-          }
-          k_point<P, T, CT, MODE, 1, 2><<<L.nitems, POINT_THREADS, smem_pre, st>>>(
-              L.items, L.run_begin, L.run_cell, L.run_order, xs, pl->n, pl->y_sorted, v, u, L.geom, L.pre);
-          SPS_CHECK_LAUNCH("point operator");
-          if (timed) SPS_CUDA(record_event(g_prof.ev[2 * g_prof.used++ + 1], st));
-          return SPS_OK;
+        if (!done && L.lanes_r == 2) {
+          static std::atomic<unsigned long long> a12{0};
+          rc = launch_k(k_point<P, T, CT, MODE, 1, 2>, a12, L.nitems, smem_pre, st, L.items, L.run_begin, L.run_cell,
+                        L.run_order, xs, pl->n, (const double*)pl->y_sorted, v, u, L.geom, pl->err_flag,
+                        (const double*)L.pre);
+          done = true;
         }
       }
-      k_point<P, T, CT, MODE, 1><<<L.nitems, POINT_THREADS, smem_pre, st>>>(
-          L.items, L.run_begin, L.run_cell, L.run_order, xs, pl->n, pl->y_sorted, v, u, L.geom, L.pre);
-      SPS_CHECK_LAUNCH("point operator");
-      if (timed) SPS_CUDA(record_event(g_prof.ev[2 * g_prof.used++ + 1], st));
-      return SPS_OK;
-    }
-  }
-  // FP32: two register layouts per run -- R = 2 dimensions in a lane's
-  // registers (4^(P-2) lanes per run, 16 accumulators each) or R = 3
-  // (4^(P-3) lanes, 64 accumulators).  P = 3 defaults to R = 2 (more resident
-  // warps); the autotuner may pick either for the apply of P = 3 and P = 4.
-  constexpr bool TWO_LAYOUTS = sizeof(T) == 4 && (P == 3 || (P == 4 && MODE == PT_APPLY));
-  const int rsel = L.lanes_r ? L.lanes_r : (P == 3 ? 2 : 3);
-  if (TWO_LAYOUTS && (rsel == 2 || (P == 3 && MODE != PT_APPLY))) {
-    if constexpr (TWO_LAYOUTS) {
-      static bool attr_r2 = false;
-      if (!attr_r2) {
-        SPS_CUDA(cudaFuncSetAttribute(k_point<P, T, CT, MODE, false, 2>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)POINT_SMEM_MAX));
-        attr_r2 = true;
+      if (!done) {
+        static std::atomic<unsigned long long> a1{0};
+        rc = launch_k(k_point<P, T, CT, MODE, 1>, a1, L.nitems, smem_pre, st, L.items, L.run_begin, L.run_cell,
+                      L.run_order, xs, pl->n, (const double*)pl->y_sorted, v, u, L.geom, pl->err_flag,
+                      (const double*)L.pre);
+        done = true;
       }
-      k_point<P, T, CT, MODE, false, 2><<<L.nitems, POINT_THREADS, smem, st>>>(
-          L.items, L.run_begin, L.run_cell, L.run_order, xs, pl->n, pl->y_sorted, v, u, L.geom);
     }
-  } else {
-    k_point<P, T, CT, MODE><<<L.nitems, POINT_THREADS, smem, st>>>(L.items, L.run_begin, L.run_cell, L.run_order,
-                                                                   xs, pl->n, pl->y_sorted, v, u, L.geom);
   }
-  SPS_CHECK_LAUNCH("point operator");
+  if (!done) {
+    // FP32: two register layouts per run -- R = 2 dimensions in a lane's
+    // registers (4^(P-2) lanes per run, 16 accumulators each) or R = 3
+    // (4^(P-3) lanes, 64 accumulators).  P = 3 defaults to R = 2 (more resident
+    // warps); the autotuner may pick either for the apply of P = 3 and P = 4.
+    constexpr bool TWO_LAYOUTS = sizeof(T) == 4 && (P == 3 || (P == 4 && MODE == PT_APPLY));
+    const int rsel = L.lanes_r ? L.lanes_r : (P == 3 ? 2 : 3);
+    bool launched = false;
+    if constexpr (TWO_LAYOUTS) {
+      if (rsel == 2 || (P == 3 && MODE != PT_APPLY)) {
+        static std::atomic<unsigned long long> ar2{0};
+        rc = launch_k(k_point<P, T, CT, MODE, 0, 2>, ar2, L.nitems, smem, st, L.items, L.run_begin, L.run_cell,
+                      L.run_order, xs, pl->n, (const double*)pl->y_sorted, v, u, L.geom, pl->err_flag,
+                      (const double*)nullptr);
+        launched = true;
+      }
+    }
+    if (!launched) {
+      static std::atomic<unsigned long long> a0{0};
+      rc = launch_k(k_point<P, T, CT, MODE>, a0, L.nitems, smem, st, L.items, L.run_begin, L.run_cell, L.run_order,
+                    xs, pl->n, (const double*)pl->y_sorted, v, u, L.geom, pl->err_flag, (const double*)nullptr);
+    }
+  }
+  if (rc != SPS_OK) return rc;
   if (timed) SPS_CUDA(record_event(g_prof.ev[2 * g_prof.used++ + 1], st));
   return SPS_OK;
 }

@@ -26,13 +26,13 @@ struct KeyParams {
 };
 
 template <typename CT>
-__global__ void k_keys(const CT* __restrict__ x, long long n, KeyParams kp,
+__global__ void k_keys(const CT* __restrict__ x, const CT* __restrict__ y, long long n, KeyParams kp,
                        unsigned long long* __restrict__ keys, unsigned int* __restrict__ perm,
                        int* __restrict__ err) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     unsigned int c[MAXP];
-    bool bad = false;
+    bool bad = !isfinite((double)y[i]);   // a non-finite response would make Phi'y non-finite
     for (int p = 0; p < kp.P; ++p) {
       CT xv = x[i * kp.P + p];
       double xd = (double)xv;
@@ -44,7 +44,7 @@ __global__ void k_keys(const CT* __restrict__ x, long long n, KeyParams kp,
       if (ci < 0) ci = 0;
       c[p] = (unsigned int)ci;
     }
-    if (bad) atomicOr(err, 1);
+    if (bad) atomicOr(err, ERR_DOMAIN);
     unsigned long long key = 0;
     for (int b = kp.L - 1; b >= 0; --b)
       for (int p = 0; p < kp.P; ++p) key = (key << 1) | (unsigned long long)((c[p] >> b) & 1u);
@@ -302,13 +302,9 @@ __global__ void k_permute_items(const WorkItem* __restrict__ in, const unsigned 
 
 int ensure_seg(sps_plan* pl, long long need) {
   if (pl->seg_cap >= need) return SPS_OK;
-  if (pl->seg_tmp) cudaFree(pl->seg_tmp);
-  pl->seg_tmp = nullptr;
+  pfree(pl, pl->seg_tmp);
   pl->seg_cap = 0;
-  if (cudaMalloc(&pl->seg_tmp, sizeof(int) * need) != cudaSuccess) {
-    set_error("allocation of segment scratch failed");
-    return SPS_ENOMEM;
-  }
+  SPS_TRY(palloc(pl, &pl->seg_tmp, need));
   pl->seg_cap = need;
   return SPS_OK;
 }
@@ -328,7 +324,7 @@ int grid_blocks(long long n, int threads) {
   return (int)b;
 }
 
-int compute_keys(sps_plan* pl, const void* x_dev, int dtype, cudaStream_t st) {
+int compute_keys(sps_plan* pl, const void* x_dev, const void* y_dev, int dtype, cudaStream_t st) {
   KeyParams kp;
   kp.P = pl->P;
   kp.L = pl->Lbits;
@@ -341,9 +337,11 @@ int compute_keys(sps_plan* pl, const void* x_dev, int dtype, cudaStream_t st) {
   SPS_CUDA(cudaMemsetAsync(pl->err_flag, 0, sizeof(int), st));
   int blocks = grid_blocks(pl->n, 256);
   if (dtype == SPS_F64)
-    k_keys<double><<<blocks, 256, 0, st>>>((const double*)x_dev, pl->n, kp, pl->keys, pl->perm, pl->err_flag);
+    k_keys<double><<<blocks, 256, 0, st>>>((const double*)x_dev, (const double*)y_dev, pl->n, kp, pl->keys,
+                                           pl->perm, pl->err_flag);
   else
-    k_keys<float><<<blocks, 256, 0, st>>>((const float*)x_dev, pl->n, kp, pl->keys, pl->perm, pl->err_flag);
+    k_keys<float><<<blocks, 256, 0, st>>>((const float*)x_dev, (const float*)y_dev, pl->n, kp, pl->keys, pl->perm,
+                                          pl->err_flag);
   SPS_CHECK_LAUNCH("keys");
   return SPS_OK;
 }
@@ -353,13 +351,9 @@ int radix_sort(sps_plan* pl, int nbits, cudaStream_t st) {
   const int ntiles = (int)((n + RS_TILE - 1) / RS_TILE);
   const long long hsize = (long long)RS_BINS * ntiles;
   if (pl->sort_hist_cap < hsize) {
-    if (pl->sort_hist) cudaFree(pl->sort_hist);
-    pl->sort_hist = nullptr;
+    pfree(pl, pl->sort_hist);
     pl->sort_hist_cap = 0;
-    if (cudaMalloc(&pl->sort_hist, sizeof(unsigned int) * hsize) != cudaSuccess) {
-      set_error("allocation of sort histogram failed");
-      return SPS_ENOMEM;
-    }
+    SPS_TRY(palloc(pl, &pl->sort_hist, hsize));
     pl->sort_hist_cap = hsize;
   }
   unsigned long long *kin = pl->keys, *kout = pl->keys_tmp;
@@ -415,20 +409,14 @@ int build_level_work(sps_plan* pl, int g, cudaStream_t st) {
   SPS_CUDA(cudaMemcpyAsync(&nruns, run_off + ncell, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
   SPS_CUDA(cudaStreamSynchronize(st));
   if ((int)nruns > L.run_cap) {   // grow only: cudaFree would synchronise the whole device
-    cudaFree(L.run_begin);
-    cudaFree(L.run_cell);
-    cudaFree(L.run_order);
-    L.run_begin = nullptr;
-    L.run_cell = nullptr;
-    L.run_order = nullptr;
+    pfree(pl, L.run_begin);
+    pfree(pl, L.run_cell);
+    pfree(pl, L.run_order);
     L.run_cap = 0;
     const unsigned int cap = nruns + nruns / 4 + 16;
-    if (cudaMalloc(&L.run_begin, sizeof(int) * (cap + 1)) != cudaSuccess ||
-        cudaMalloc(&L.run_cell, sizeof(unsigned long long) * cap) != cudaSuccess ||
-        cudaMalloc(&L.run_order, sizeof(int) * cap) != cudaSuccess) {
-      set_error("allocation of run lists failed");
-      return SPS_ENOMEM;
-    }
+    SPS_TRY(palloc(pl, &L.run_begin, (long long)cap + 1));
+    SPS_TRY(palloc(pl, &L.run_cell, (long long)cap));
+    SPS_TRY(palloc(pl, &L.run_order, (long long)cap));
     L.run_cap = (int)cap;
   }
   L.nruns = (int)nruns;
@@ -449,14 +437,10 @@ int build_level_work(sps_plan* pl, int g, cudaStream_t st) {
   SPS_CUDA(cudaMemcpyAsync(&nitems, item_off + ntile, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
   SPS_CUDA(cudaStreamSynchronize(st));
   if ((int)nitems > L.item_cap) {
-    cudaFree(L.items);
-    L.items = nullptr;
+    pfree(pl, L.items);
     L.item_cap = 0;
     const unsigned int cap = nitems + nitems / 4 + 16;
-    if (cudaMalloc(&L.items, sizeof(WorkItem) * cap) != cudaSuccess) {
-      set_error("allocation of work items failed");
-      return SPS_ENOMEM;
-    }
+    SPS_TRY(palloc(pl, &L.items, (long long)cap));
     L.item_cap = (int)cap;
   }
   L.nitems = (int)nitems;

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/sps.h"
@@ -118,14 +119,17 @@ struct sps_plan {
   long long sort_hist_cap = 0;
   int* seg_tmp = nullptr;       // per-segment counts / offsets
   long long seg_cap = 0;
-  int* err_flag = nullptr;      // device error flag
+  int* err_flag = nullptr;      // device error flags (ERR_* bits)
   // right-hand side Phi'y (FP64) and its norm
   double* rhs = nullptr;
   double rhs_norm = 0.0;
-  // coarse inverse (FP64 and FP32 copies)
+  // dense coarse solver: the assembled A_1, the inverse Cholesky factor Z of
+  // its Jacobi-scaled form with the scale folded in (A_1^-1 = Z'Z) and Z',
+  // each K_1 x K_1 FP64; null with the inner coarse CG (opt.coarse_cg)
+  double* coarse_A = nullptr;
   double* coarse_inv = nullptr;
-  float* coarse_inv_f = nullptr;
-  double* coarse_tmp = nullptr;   // row/column snapshots for the inversion
+  double* coarse_invt = nullptr;
+  double* coarse_tmp = nullptr;   // scale, pivots, work vectors (6 K_1) + scaled copy (K_1^2)
   // penalty and transfer temporaries (max K over levels)
   double* dtmp[8] = {nullptr};
   float* ftmp[8] = {nullptr};
@@ -149,6 +153,9 @@ struct sps_plan {
   } graph[2];
   unsigned gen = 0;
   cudaStream_t cap_stream = nullptr;
+  // device memory held by the plan (every cudaMalloc goes through plan_alloc)
+  std::unordered_map<void*, size_t> dev_sizes;
+  long long dev_bytes = 0;
 };
 
 namespace sps {
@@ -161,6 +168,9 @@ int cuda_fail(cudaError_t e, const char* what);
     cudaError_t _e = (call);                             \
     if (_e != cudaSuccess) return sps::cuda_fail(_e, #call); \
   } while (0)
+// device error flags (plan->err_flag)
+constexpr int ERR_DOMAIN = 1;     // a coordinate outside [lo, hi] or a non-finite coordinate/response
+constexpr int ERR_SMEM = 2;       // the point operator's staged points exceeded its shared memory
 // propagate a non-OK status code
 #define SPS_TRY(x)                   \
   do {                               \
@@ -175,8 +185,27 @@ void count_launches(unsigned long long k);
     SPS_CUDA(cudaGetLastError()); \
   } while (0)
 
+// ---- device memory of a plan (api.cu) ----
+// Every allocation of plan memory goes through plan_alloc, which enforces
+// sps_options.max_device_bytes and tracks the bytes held.
+int plan_alloc(sps_plan* pl, void** p, size_t bytes);
+void plan_free(sps_plan* pl, void* p);
+template <typename T>
+int palloc(sps_plan* pl, T** p, long long count) {
+  if (count < 1) count = 1;
+  return plan_alloc(pl, (void**)p, sizeof(T) * (size_t)count);
+}
+template <typename T>
+void pfree(sps_plan* pl, T*& p) {
+  plan_free(pl, (void*)p);
+  p = nullptr;
+}
+// Reads and clears the device error flags; SPS_EINTERNAL if the point
+// operator reported an inconsistent launch.
+int check_device_errors(sps_plan* pl, cudaStream_t st);
+
 // ---- sort.cu ----
-int compute_keys(sps_plan* pl, const void* x_dev, int dtype, cudaStream_t st);
+int compute_keys(sps_plan* pl, const void* x_dev, const void* y_dev, int dtype, cudaStream_t st);
 int radix_sort(sps_plan* pl, int nbits, cudaStream_t st);
 int gather_points(sps_plan* pl, const void* x_dev, const void* y_dev, int dtype, cudaStream_t st);   // also fills x32_sorted
 int build_level_work(sps_plan* pl, int g, cudaStream_t st);
@@ -216,7 +245,11 @@ int stencil_assemble(sps_plan* pl, int g, cudaStream_t st);
 template <typename T>
 int stencil_apply(sps_plan* pl, int g, const T* v, T* u, cudaStream_t st);
 template <typename T>
-int coarse_solve(sps_plan* pl, const T* r, T* e, cudaStream_t st);
+int coarse_solve(sps_plan* pl, const T* r, T* e, cudaStream_t st);   // dense inverse (+ refinement in FP64)
+// Inner Jacobi-preconditioned CG on level 1 from e = 0, opt.coarse_iters
+// iterations; r1, p1 are level-1 work vectors distinct from the penalty temporaries.
+template <typename T>
+int coarse_cg(sps_plan* pl, const T* b, T* e, T* r1, T* p1, cudaStream_t st);
 
 // elementwise / reductions
 template <typename T>

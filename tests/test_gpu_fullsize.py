@@ -1,6 +1,10 @@
 """The CUDA path at the full sizes of the workloads, in the launch
 configuration bench.py times, checked on outputs the oracle can compute one
 coefficient at a time and on properties that hold at any size."""
+import hashlib
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -56,6 +60,56 @@ def test_scale_apply_sampled(scale, prec, tol):
     ks = _sample_coefficients(pr, plan, 64, 4)
     ref = sampled.apply_rows(pr.x, v, ks, pr.lo, pr.hi, pr.intervals, 3, pr.lam)
     assert np.max(np.abs(u[ks] - ref)) <= tol * np.max(np.abs(u))
+
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _scale_golden(pr):
+    """The oracle's solution of the scale workload (tier-2 MG-PCG to rel.res
+    1e-15, written by tests/golden/make_scale_alpha.py) and its record; the
+    inputs must be bit-identical to the ones it was computed from."""
+    rec = json.load(open(os.path.join(GOLDEN, "scale_alpha.json")))
+    sha = lambda a: hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest()
+    assert rec["x_sha256"] == sha(pr.x) and rec["y_sha256"] == sha(pr.y), "scale inputs differ from the golden's"
+    return np.load(os.path.join(GOLDEN, "scale_alpha.npy")), rec
+
+
+def test_scale_fp64_coefficients_match_oracle(scale):
+    """The FP64 solve of the full scale workload (P = 3, 64^3 intervals, K =
+    300,763, 10^6 clustered points) at tol 1e-13 equals the oracle's converged
+    coefficients to 1e-8 relative (max norm); at the benchmark tolerance 1e-8
+    the remaining iteration error is reported."""
+    pr, plan = scale
+    ref, rec = _scale_golden(pr)
+    coef = torch.zeros(plan.K, dtype=torch.float64, device="cuda")
+    _, res = plan.solve(1e-13, coef)
+    err = rel_err(coef.cpu().numpy(), ref)
+    _, res8 = plan.solve(pr.tol, coef)
+    err8 = rel_err(coef.cpu().numpy(), ref)
+    print("scale FP64: tol 1e-13: %d iterations, max rel. coefficient error %.2e; tol 1e-8: %d iterations, %.2e "
+          "(oracle: %d iterations to 1e-8)" % (res.iterations, err, res8.iterations, err8, rec["iterations_to_1e-8"]))
+    assert res.status == B.SPS_OK and err < 1e-8
+    assert err8 < 1e-3
+
+
+def test_scale_mixed_coefficients_match_oracle(scale):
+    """Mixed precision (FP32 V-cycle and operator in the FP64 flexible PCG) on
+    the full scale workload: at tol 1e-12 within 1e-7 of the oracle's
+    coefficients; the error at the benchmark tolerance is reported."""
+    pr, plan = scale
+    ref, _ = _scale_golden(pr)
+    with B.Plan(pr.P, pr.intervals, pr.levels, pr.lam, pr.lo, pr.hi, precision=B.SPS_PREC_MIXED) as pm:
+        pm.set_points(_device(pr.x), _device(pr.y))
+        c = torch.zeros(plan.K, dtype=torch.float64, device="cuda")
+        _, res = pm.solve(1e-12, c)
+        err = rel_err(c.cpu().numpy(), ref)
+        _, res8 = pm.solve(pr.tol, c)
+        err8 = rel_err(c.cpu().numpy(), ref)
+    print("scale mixed: tol 1e-12: %d iterations, max rel. coefficient error %.2e; tol 1e-8: %d iterations, %.2e"
+          % (res.iterations, err, res8.iterations, err8))
+    assert res.status == B.SPS_OK and err < 1e-7
+    assert err8 < 1e-3
 
 
 def test_scale_solve_residual_by_oracle(scale):

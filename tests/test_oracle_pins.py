@@ -445,3 +445,52 @@ def test_pins_catch_planted_mistakes(monkeypatch):
     monkeypatch.setattr(spline, "strides", first_fastest)
     with pytest.raises(AssertionError):
         test_phi_tensor_order_unequal_grids()
+
+
+# ------------------------------------------------------------------ Jacobi spectrum, Lanczos branch
+
+def _lmax_case(P, intervals, n, lam, seed):
+    r = np.random.default_rng(seed)
+    x = r.random((n, P))
+    y = np.sin(3.0 * x[:, 0]) + 0.1 * r.standard_normal(n)
+    A, _, _, _ = spline.system(x, y, [0.0] * P, [1.0] * P, intervals, 3, lam)
+    return A
+
+
+@pytest.mark.parametrize("P,intervals,n,lam", [(3, [8, 16, 8], 6007, 3e-3), (4, [4, 8, 4, 4], 4001, 1e-1)])
+def test_lambda_max_jacobi_lanczos_branch(P, intervals, n, lam):
+    """lambda_max(D^-1 A) by the oracle's Lanczos branch (K > 2000) against
+    the dense symmetric eigensolver on D^-1/2 A D^-1/2, and two facts that hold
+    for any SPD A: it is at least the largest Rayleigh quotient of D^-1 A over
+    the unit vectors (which is 1) and at most the largest absolute row sum of
+    D^-1 A (Gershgorin)."""
+    A = _lmax_case(P, intervals, n, lam, seed=100 + P)
+    K = A.shape[0]
+    assert K > 2000          # the eigsh branch
+    Dinv = 1.0 / A.diagonal()
+    lm = mgcg.lambda_max_jacobi(A, Dinv)
+    s = np.sqrt(Dinv)
+    dense = np.linalg.eigvalsh(s[:, None] * A.toarray() * s[None, :])[-1]
+    assert abs(lm - dense) <= 1e-9 * dense
+    gersh = float(np.max(np.abs(A).sum(axis=1).A1 * Dinv))
+    assert 1.0 <= lm <= gersh * (1 + 1e-12)
+    # a planted mistake -- the spectrum of A instead of D^-1 A -- fails the first check
+    wrong = float(spla.eigsh(A, k=1, which="LA", return_eigenvectors=False, tol=1e-10)[0])
+    assert abs(wrong - dense) > 1e-3 * dense
+
+
+# ------------------------------------------------------------------ tier-2 oracle (assembled MG-PCG)
+
+def test_tier2_mgcg_matches_direct_on_clustered_cut():
+    """The assembled Galerkin MG-PCG used for the large workloads (Algorithm 8
+    with Galerkin coarse operators I' A I) reaches the direct solve on a cut of
+    the clustered P = 3 workload: 2e4 of its points on 16^3 intervals (K =
+    6859), 4 levels."""
+    import workloads as W
+    pr = W.scale(n=20000)
+    res = mgcg.solve_tier2(pr.x, pr.y, pr.lo, pr.hi, [16, 16, 16], 3, pr.lam, 4, tol=1e-13)
+    A, b, _, _ = spline.system(pr.x, pr.y, pr.lo, pr.hi, [16, 16, 16], 3, pr.lam)
+    ref = mgcg.solve_direct(A, b)
+    assert res.rel_res <= 1e-13
+    assert np.linalg.norm(b - A @ res.alpha) / np.linalg.norm(b) <= 2e-13
+    assert np.max(np.abs(res.alpha - ref)) <= 1e-8 * np.max(np.abs(ref))

@@ -9,13 +9,22 @@ method.
 Generator: SplitMix64 (Steele, Lea and Flood, "Fast splittable pseudorandom
 number generators", OOPSLA 2014) used in counter mode, so the i-th draw of a
 stream is mix(key + (i+1) * GAMMA).  Uniform doubles take the top 53 bits;
-normals use the Box-Muller transform.  Everything is plain numpy uint64
-arithmetic, identical on x86_64 and aarch64.
+normals use the Box-Muller transform.
+
+Bit-identical on x86_64 and aarch64: besides numpy uint64 arithmetic, the
+recipes use only IEEE-754 basic operations (+, -, *, /, sqrt, frexp/ldexp,
+rint), each correctly rounded, in a fixed order.  numpy's own log/exp/sin/cos
+are vectorised differently per CPU and may differ in the last bit, so the
+logarithm, exponential, sine and cosine below are evaluated from their power
+series after an exact argument reduction (accurate to a few units in the last
+place; what matters here is that both machines draw the same numbers), and
+sums over coordinates are written out instead of reduced by numpy.
 """
 from __future__ import annotations
 
 import math
 from dataclasses import dataclass, field
+from decimal import Decimal
 
 import numpy as np
 
@@ -32,6 +41,89 @@ def _mix(z: np.ndarray) -> np.ndarray:
     z *= _M2
     z ^= z >> np.uint64(31)
     return z
+
+
+# ---------------------------------------------------------------- portable elementary functions
+
+_LN2_DEC = "0.69314718055994530941723212145817656807550013436"   # ln 2 to 47 digits
+_LN2 = float(_LN2_DEC)                    # the double nearest ln 2
+_LN2_HI = 2977044472.0 / 4294967296.0     # ln 2 to 32 bits: k * _LN2_HI is exact for |k| < 2^21
+_LN2_LO = float(Decimal(_LN2_DEC) - Decimal(2977044472) / Decimal(4294967296))   # the rest, rounded once
+_SQRT_HALF = 0.7071067811865476
+_TWO_PI = 6.283185307179586
+
+
+def _horner(c: list, z: np.ndarray) -> np.ndarray:
+    acc = np.full_like(z, c[-1])
+    for a in reversed(c[:-1]):
+        acc = acc * z + a
+    return acc
+
+
+def plog(u: np.ndarray) -> np.ndarray:
+    """Natural logarithm of u > 0: u = m 2^e with m in [sqrt(1/2), sqrt(2)),
+    log m = 2 atanh(s), s = (m - 1)/(m + 1), |s| < 0.172, by 14 terms of the
+    atanh series."""
+    u = np.asarray(u, dtype=np.float64)
+    m, e = np.frexp(u)
+    low = m < _SQRT_HALF
+    m = np.where(low, m * 2.0, m)
+    e = np.where(low, e - 1, e).astype(np.float64)
+    s = (m - 1.0) / (m + 1.0)
+    poly = _horner([1.0 / (2 * k + 1) for k in range(14)], s * s)
+    return e * _LN2 + 2.0 * s * poly
+
+
+def pexp(x: np.ndarray) -> np.ndarray:
+    """e^x: x = k ln 2 + r with |r| <= ln2 / 2 (two-part ln 2), e^r by 18 terms
+    of its series, scaled by 2^k."""
+    x = np.asarray(x, dtype=np.float64)
+    k = np.rint(x / _LN2)
+    k = np.clip(k, -1100.0, 1100.0)
+    r = (x - k * _LN2_HI) - k * _LN2_LO
+    p = _horner([1.0 / math.factorial(j) for j in range(18)], r)
+    return np.ldexp(p, k.astype(np.int64))
+
+
+def _sincos_reduced(t: np.ndarray):
+    """t in turns: t = q/4 + r, |r| <= 1/8 (exact for |t| <= 2^50); returns
+    (sin 2 pi r, cos 2 pi r, q mod 4) by 12-term series."""
+    t = np.asarray(t, dtype=np.float64)
+    k = np.rint(4.0 * t)
+    r = t - k * 0.25
+    x = r * _TWO_PI
+    z = x * x
+    c = _horner([(-1.0) ** j / math.factorial(2 * j) for j in range(12)], z)
+    sn = x * _horner([(-1.0) ** j / math.factorial(2 * j + 1) for j in range(12)], z)
+    return sn, c, np.mod(k, 4.0)
+
+
+def psin_turns(t: np.ndarray) -> np.ndarray:
+    """sin(2 pi t)."""
+    sn, c, q = _sincos_reduced(t)
+    return np.select([q == 0, q == 1, q == 2], [sn, c, -sn], -c)
+
+
+def pcos_turns(t: np.ndarray) -> np.ndarray:
+    """cos(2 pi t)."""
+    sn, c, q = _sincos_reduced(t)
+    return np.select([q == 0, q == 1, q == 2], [c, -sn, -c], sn)
+
+
+def _sq_dist(x: np.ndarray, c) -> np.ndarray:
+    """|x_i - c|^2, summed over the coordinates in order."""
+    d = x[:, 0] - c[0]
+    r2 = d * d
+    for p in range(1, x.shape[1]):
+        d = x[:, p] - c[p]
+        r2 = r2 + d * d
+    return r2
+
+
+def _log_uniform(lo: float, hi: float, u: float) -> float:
+    """exp(log lo + u (log hi - log lo)) with the portable functions."""
+    a, b = plog(np.array([lo, hi]))
+    return float(pexp(np.array([a + u * (b - a)]))[0])
 
 
 def _stream_key(seed: int, stream: int) -> np.uint64:
@@ -58,7 +150,7 @@ def normal(seed: int, stream: int, count: int) -> np.ndarray:
     u = uniform(seed, stream, 2 * count)
     u1 = 1.0 - u[:count]          # (0, 1]
     u2 = u[count:]
-    return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * math.pi * u2)
+    return np.sqrt(-2.0 * plog(u1)) * pcos_turns(u2)
 
 
 @dataclass
@@ -96,7 +188,7 @@ def uniform_points(seed: int, stream: int, n: int, P: int) -> np.ndarray:
 def pr1(seed: int = 0, n: int = 2000) -> Problem:
     """P=2, 16 intervals, n=2000 uniform, y = sin(2 pi x1) cos(2 pi x2) + N(0, 0.1^2)."""
     x = uniform_points(seed, 1, n, 2)
-    y = np.sin(2 * math.pi * x[:, 0]) * np.cos(2 * math.pi * x[:, 1]) + 0.1 * normal(seed, 2, n)
+    y = psin_turns(x[:, 0]) * pcos_turns(x[:, 1]) + 0.1 * normal(seed, 2, n)
     return Problem("pr1", 2, 3, [16, 16], 3, 1e-3, 1e-10, x, y, [0.0] * 2, [1.0] * 2)
 
 
@@ -117,8 +209,8 @@ def gaussian_mixture_points(seed: int, n: int, P: int, comps: int = 3) -> np.nda
 def scale(seed: int = 1, n: int = 1_000_000) -> Problem:
     """P=3, 64 intervals, clustered mixture, y = exp(-|x-0.5|^2/0.05) + N(0, 0.05^2)."""
     x = gaussian_mixture_points(seed, n, 3)
-    r2 = np.sum((x - 0.5) ** 2, axis=1)
-    y = np.exp(-r2 / 0.05) + 0.05 * normal(seed, 14, n)
+    r2 = _sq_dist(x, [0.5] * 3)
+    y = pexp(-r2 / 0.05) + 0.05 * normal(seed, 14, n)
     return Problem("scale", 3, 3, [64, 64, 64], 6, 1e-4, 1e-8, x, y, [0.0] * 3, [1.0] * 3)
 
 
@@ -126,7 +218,10 @@ def mixed(seed: int = 2, n: int = 4_000_000) -> Problem:
     """P=4, 32 intervals, n uniform stored as FP32, y = prod sin(pi x_d) + N(0, 0.1^2)."""
     x = uniform_points(seed, 1, n, 4).astype(np.float32)
     xd = x.astype(np.float64)
-    y = (np.prod(np.sin(math.pi * xd), axis=1) + 0.1 * normal(seed, 2, n)).astype(np.float32)
+    f = psin_turns(0.5 * xd[:, 0])
+    for p in range(1, 4):
+        f = f * psin_turns(0.5 * xd[:, p])
+    y = (f + 0.1 * normal(seed, 2, n)).astype(np.float32)
     return Problem("mixed", 4, 3, [32] * 4, 5, 1e-3, 1e-10, x, y, [0.0] * 4, [1.0] * 4,
                    precision="mixed")
 
@@ -139,8 +234,8 @@ def bumps_response(seed: int, stream: int, x: np.ndarray, noise: float = 0.05) -
     cen = uniform(seed, stream + 2, 3 * P).reshape(3, P)
     y = np.zeros(n)
     for b in range(3):
-        r2 = np.sum((x - cen[b]) ** 2, axis=1)
-        y += amp[b] * np.exp(-r2 / (2.0 * wid[b] ** 2))
+        r2 = _sq_dist(x, cen[b])
+        y += amp[b] * pexp(-r2 / (2.0 * (wid[b] * wid[b])))
     return y + noise * normal(seed, stream + 3, n)
 
 
@@ -165,8 +260,8 @@ def batched(seed: int = 3, count: int = 512, n_lo: float = 1e3, n_hi: float = 1e
         P = 1 + min(int(r[k, 0] * 3), 2)
         grids = [N for N in BATCH_GRIDS[P] if (N + 3) ** P <= max_coef]
         N = grids[min(int(r[k, 1] * len(grids)), len(grids) - 1)]
-        n = int(round(math.exp(math.log(n_lo) + r[k, 2] * (math.log(n_hi) - math.log(n_lo)))))
-        lam = math.exp(math.log(1e-5) + r[k, 3] * (math.log(1e-1) - math.log(1e-5)))
+        n = int(round(_log_uniform(n_lo, n_hi, r[k, 2])))
+        lam = _log_uniform(1e-5, 1e-1, r[k, 3])
         x = uniform_points(seed, 1000 + 8 * k, n, P)
         y = bumps_response(seed, 1001 + 8 * k, x)
         probs.append(Problem(f"batch{k}", P, 3, [N] * P, levels_for(N), lam, 1e-8, x, y,
@@ -193,14 +288,14 @@ def serving_trace(seed: int = 4, count: int = 2000, rate: float = 200.0, n_lo: f
     (x, y are None) so a trace can be inspected cheaply.
     """
     r = uniform(seed, 200, 5 * count).reshape(count, 5)
-    t = np.cumsum(-np.log(1.0 - r[:, 0]) / rate)
+    t = np.cumsum(-plog(1.0 - r[:, 0]) / rate)
     out = []
     for k in range(count):
         P = P_choices[min(int(r[k, 1] * len(P_choices)), len(P_choices) - 1)]
         grids = SERVE_GRIDS[P]
         N = grids[min(int(r[k, 2] * len(grids)), len(grids) - 1)]
-        n = int(round(math.exp(math.log(n_lo) + r[k, 3] * (math.log(n_hi) - math.log(n_lo)))))
-        lam = math.exp(math.log(1e-5) + r[k, 4] * (math.log(1e-2) - math.log(1e-5)))
+        n = int(round(_log_uniform(n_lo, n_hi, r[k, 3])))
+        lam = _log_uniform(1e-5, 1e-2, r[k, 4])
         if materialize:
             x = uniform_points(seed, 5000 + 8 * k, n, P)
             y = bumps_response(seed, 5001 + 8 * k, x)
@@ -216,5 +311,5 @@ def paper_sigmoid(seed: int, n: int, P: int) -> tuple:
     f_P(x) = 1 / (1 + exp(-16 (|x|^2 / P - 0.5))) (the bounded reading of the
     sigmoid; the printed denominator 1 - exp(...) has a pole)."""
     x = uniform_points(seed, 1, n, P)
-    f = 1.0 / (1.0 + np.exp(-16.0 * (np.sum(x * x, axis=1) / P - 0.5)))
+    f = 1.0 / (1.0 + pexp(-16.0 * (_sq_dist(x, [0.0] * P) / P - 0.5)))
     return x, f + 0.1 * normal(seed, 2, n)
