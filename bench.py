@@ -206,14 +206,19 @@ class OracleSolveTiming:
         self.iters, self.iters_src = oracle_iterations(pr)
         ns = min(pr.n, n_sample)
         xs, ys = pr.x[:ns], pr.y[:ns]
-        t0 = time.perf_counter()
-        spline.system(xs, ys, pr.lo, pr.hi, pr.intervals, pr.q, pr.lam)
-        t_sys = time.perf_counter() - t0
+        # assembly time a + b n from two sample sizes, extrapolated to all n
+        t_sys = []
+        for m in (ns // 2, ns):
+            t0 = time.perf_counter()
+            spline.system(xs[:m], ys[:m], pr.lo, pr.hi, pr.intervals, pr.q, pr.lam)
+            t_sys.append(time.perf_counter() - t0)
+        per_point = max(t_sys[1] - t_sys[0], 0.0) / (ns - ns // 2)
         t0 = time.perf_counter()
         self.H = mgcg.build_hierarchy(xs, ys, pr.lo, pr.hi, pr.intervals, pr.q, pr.lam, pr.levels, omega=0.5,
                                       galerkin=True)
         t_build = time.perf_counter() - t0
-        self.setup_s = t_build + t_sys * (pr.n / ns - 1.0)
+        t_sys = t_sys[1]
+        self.setup_s = t_build + per_point * (pr.n - ns)
         self.sample = ns
         self.t_sys, self.t_build = t_sys, t_build
 
@@ -242,7 +247,8 @@ class OracleSolveTiming:
             return ("oracle tier-1 direct solve (sparse assembly + LAPACK banded Cholesky) of the whole workload, "
                     "timed whole; single-threaded assembly, LAPACK threads as the host's BLAS sets")
         return ("oracle tier-2 MG-PCG (assembled matrices, Galerkin coarse operators): set-up %.1f s (hierarchy on "
-                "%d of %d points %.1f s, Phi/Phi'Phi assembly %.1f s scaled to all points) + %d iterations "
+                "%d of %d points %.1f s; Phi/Phi'Phi assembly, %.1f s there, extrapolated linearly in n from two "
+                "sample sizes to all points) + %d iterations "
                 "(the oracle's own count to rel.res 1e-8, from %s) x %.3f s per iteration timed at the full K; "
                 "single-threaded sparse products" % (self.setup_s, self.sample, self.pr.n, self.t_build, self.t_sys,
                                                      self.iters, os.path.relpath(self.iters_src, ROOT), self.iter_s))
