@@ -619,6 +619,8 @@ def run_paper(args):
                              "status": res.status}
         return out
 
+    if args.paper_sweep:
+        return run_paper_sweep(args, lam, tol, paper)
     table2 = {P: run(P, 5) for P in (1, 2, 3, 4)}
     fig2 = {G: run(2, G) for G in (4, 5, 6, 7)}
     # Table 3 / Fig. 3: condition numbers of A_G and C_MG A_G at P = 2, G = 5 (K = 1225)
@@ -634,6 +636,43 @@ def run_paper(args):
             "table2_gpu": table2, "fig2_gpu_P2": fig2,
             "table2_paper_iterations_cg_mgcg": paper, "table3_gpu": table3}
     print(json.dumps(line), flush=True)
+
+
+def run_paper_sweep(args, lam, tol, paper):
+    """Section 4 with the smoothing parameters the paper does not state: for
+    nu1 = nu2 in {1, 2, 3} and the damping omega = f * 4 / (3 lambda_max(D^-1 A))
+    with f in {0.5, 0.75, 1, 1.25, 1.4}: the condition number of C_MG A_G at
+    P = 2, G = 5 (Table 3, printed 1.82) and the MGCG iteration counts of
+    Table 2 (P = 1..4, G = 5; printed 2 / 4 / 14 / 19), on the same data."""
+    import torch
+
+    from paper_1901_00654_gb300 import analysis
+    from paper_1901_00654_gb300 import binding as B
+    from paper_1901_00654_gb300 import build as libbuild
+    libbuild.build_library()
+    data = {P: W.paper_sigmoid(5, 100_000, P) for P in (1, 2, 3, 4)}
+    rows = []
+    for nu in (1, 2, 3):
+        for f in (0.5, 0.75, 1.0, 1.25, 1.4):
+            row = {"nu1": nu, "nu2": nu, "omega_factor": f, "iterations": {}}
+            for P in (1, 2, 3, 4):
+                x, y = data[P]
+                with B.Plan(P, [32] * P, 5, lam, nu1=nu, nu2=nu, max_iter=50000) as pl:
+                    pl.set_points(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda())
+                    om = B.sps_get_omega(pl.h, 5)
+                    B.sps_set_omega(pl.h, [max(o * f, 1e-12) if o > 0 else 1.0 for o in om])
+                    coef = torch.zeros(pl.K, dtype=torch.float64, device="cuda")
+                    _, res = pl.solve(tol, coef, check=False)
+                    row["iterations"][P] = res.iterations
+                    if P == 2:
+                        sp = analysis.spectra(*analysis.operator_matrices(pl, 5))
+                        row["kappa_MG_A_P2"] = sp["kappa_MA"]
+                        row["eig_MG_A_min_max"] = [float(sp["eig_MA"][0]), float(sp["eig_MA"][-1])]
+            rows.append(row)
+            print(json.dumps(row), flush=True)
+    print(json.dumps({"workload": "paper Section 4 sweep: n=1e5 sigmoid data, lambda=%g, rel.res %g" % (lam, tol),
+                      "table3_paper_kappa_MG_JAC_A": 1.82, "table2_paper_iterations_cg_mgcg": paper,
+                      "sweep": rows}), flush=True)
 
 
 def run_batched(args):
@@ -657,6 +696,19 @@ def run_batched(args):
     coefs = [torch.zeros(pl.K, dtype=torch.float64, device="cuda") for pl in plans]
     hs = [pl.h for pl in plans]
     tol = args.batch_tol
+    # the default shape (clusters of 2 for the costliest problems), then the autotuner's pick
+    default_s = []
+    for _ in range(max(args.warmup, 1)):
+        B.sps_solve_batch_shape(hs, coefs, tol, cluster=2, check=False)
+    for _ in range(max(1, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        B.sps_solve_batch_shape(hs, coefs, tol, cluster=2, check=False)
+        torch.cuda.synchronize()
+        default_s.append(time.perf_counter() - t0)
+    t0 = time.perf_counter()
+    tuned = B.sps_tune_batch(hs, coefs, tol)
+    tune_s = time.perf_counter() - t0
     for _ in range(max(args.warmup, 1)):
         B.sps_solve_batch(hs, coefs, tol, check=False)
     times = []
@@ -693,6 +745,9 @@ def run_batched(args):
             "cta_ms_per_problem": {"max": cta_ms[0], "top5": cta_ms[:5], "sum": sum(cta_ms),
                                    "median": statistics.median(cta_ms)},
             "setup_s_all_plans": setup_s,
+            "autotuned_shape": {"cluster": tuned[0], "big": tuned[1], "simulated_ms": tuned[2],
+                                "tuning_s": tune_s},
+            "default_shape_cluster2_solves_per_s": len(probs) / statistics.median(default_s),
             "sequential_plain_fp64": {"solves_per_s": seq_n / seq_t, "sample": seq_n}}
     print(json.dumps(line), flush=True)
 
@@ -775,6 +830,8 @@ def main():
     ap.add_argument("--serve-max-iter", type=int, default=1500)
     ap.add_argument("--serve-seq-sample", type=int, default=6)
     ap.add_argument("--sweep", action="store_true", help="with --apply-only: every tile side and lane layout")
+    ap.add_argument("--paper-sweep", action="store_true",
+                    help="with --config paper: nu1 = nu2 in {1,2,3} x damping factors (Table 3 / Table 2)")
     ap.add_argument("--tile", type=int, default=0, help="with --apply-only: fixed tile side (no autotuning)")
     ap.add_argument("--lanes-r", type=int, default=0, help="with --apply-only --tile: fixed lane layout")
     ap.add_argument("--slots", type=int, default=8)

@@ -197,23 +197,51 @@ SPS_API int sps_destroy(sps_plan* plan);
 /* Thread-local message of the last failure (never NULL). */
 SPS_API const char* sps_last_error(void);
 
+/* Launch shape of the batched solver (not a step of the paper's method).  The
+ * costliest problems of a batch are solved each by a thread-block cluster of
+ * `cluster` CTAs (their loops split across the CTAs, dot products through
+ * distributed shared memory), the rest by one CTA each. */
+typedef struct sps_batch_shape {
+    int    cluster;        /* CTAs per cluster: 1 (no clusters), 2, 4 or 8 */
+    int    big;            /* the `big` costliest problems go to clusters; -1: those
+                              whose cost exceeds the batch's total cost per CTA */
+    double predicted_ms;   /* sps_tune_batch: simulated batch time of this shape */
+} sps_batch_shape;
+
 /* Solve `count` independent problems in ONE persistent kernel launch captured
  * in a CUDA graph, running the mixed-precision flexible PCG of Algorithm 8
- * with the FP32 V-cycle of Algorithm 7 inside the kernel.  The CTAs form
- * thread-block clusters of 2: problems costing more than the batch's total
- * cost per CTA are taken first (largest first) from a device queue and solved
- * each by a whole cluster; then every CTA takes the remaining problems alone.
- * The environment variable SPS_BATCH_CLUSTER (1, 2, 4 or 8), read at each
- * call, sets another cluster size; 1 gives one CTA per problem throughout.
- * Results agree with sps_solve to the solve's tolerance (the summation order
- * differs).  plans[i] must have
- * P <= 3 and points set; coefs[i] receives K_G(i) doubles in `mem`; tol is
- * shared; results may be NULL (else `count` entries).  Each plan's buffers are
- * used, so a plan must not be in another call at the same time.  Returns the
- * first non-OK status among the problems (all are attempted).  Synchronises
- * `stream`. */
+ * with the FP32 V-cycle of Algorithm 7 inside the kernel.  Problems are taken
+ * from device queues in decreasing cost order: first the costliest by
+ * thread-block clusters, then the rest by single CTAs.  The shape is the one
+ * sps_tune_batch chose for a batch of the same problems (same count and, per
+ * problem, P, K and n) if it was tuned, else clusters of 2 CTAs for the problems
+ * costing more than the batch's total cost per CTA.  Results agree with
+ * sps_solve to the solve's tolerance (the summation order differs).  plans[i]
+ * must have P <= 3, the dense coarse solver and points set; coefs[i] receives
+ * K_G(i) doubles in `mem`; tol is shared; results may be NULL (else `count`
+ * entries).  Each plan's buffers are used, so a plan must not be in another
+ * call at the same time.  Returns the first non-OK status among the problems
+ * (all are attempted).  Synchronises `stream`. */
 SPS_API int sps_solve_batch(sps_plan* const* plans, int count, double* const* coefs, int mem, double tol,
                             sps_result* results, void* stream);
+
+/* sps_solve_batch with an explicit launch shape (shape may be NULL: as
+ * sps_solve_batch); *used (may be NULL) receives the shape that ran (a cluster
+ * size that cannot be resident on the device falls back to 1). */
+SPS_API int sps_solve_batch_shape(sps_plan* const* plans, int count, double* const* coefs, int mem, double tol,
+                                  const sps_batch_shape* shape, sps_result* results, sps_batch_shape* used,
+                                  void* stream);
+
+/* Autotuner of the batched solver's shape: solves the batch once for every
+ * cluster size 1, 2, 4, 8 with every problem on a team of that size, keeps
+ * each problem's measured time per size, and picks the cluster size and the
+ * number of problems solved by clusters whose simulated batch time (the two
+ * device queues replayed with the measured times) is the shortest.  The pick
+ * is returned in *best and used by later sps_solve_batch calls on the same
+ * problems; coefs receive the coefficients of the last tuning solve.
+ * Errors: as sps_solve_batch. */
+SPS_API int sps_tune_batch(sps_plan* const* plans, int count, double* const* coefs, int mem, double tol,
+                           sps_batch_shape* best, void* stream);
 
 /* Values s(x_j) = sum_k alpha_k phi_k(x_j) of the spline with coefficients
  * `coef` at m query points: Algorithm 4 (transposed Khatri-Rao product) with

@@ -32,7 +32,7 @@ EXPORTED = ["sps_default_options", "sps_plan_create", "sps_set_points", "sps_sol
             "sps_set_omega", "sps_probe_fma_rate", "sps_point_apply", "sps_launch_count",
             "sps_profile_begin", "sps_profile_end", "sps_solve_batch", "sps_set_lambda",
             "sps_penalty_apply_noalloc", "sps_get_tuning", "sps_evaluate", "sps_level_matrix",
-            "sps_plan_device_bytes"]
+            "sps_plan_device_bytes", "sps_solve_batch_shape", "sps_tune_batch"]
 
 
 class sps_options(C.Structure):
@@ -47,6 +47,10 @@ class sps_options(C.Structure):
 class sps_result(C.Structure):
     _fields_ = [("status", C.c_int), ("iterations", C.c_int), ("rel_res", C.c_double),
                 ("rel_res_true", C.c_double), ("fp64_applies", C.c_int), ("solve_ms", C.c_double)]
+
+
+class sps_batch_shape(C.Structure):
+    _fields_ = [("cluster", C.c_int), ("big", C.c_int), ("predicted_ms", C.c_double)]
 
 
 class SpsError(RuntimeError):
@@ -93,6 +97,9 @@ def load(path: str | None = None) -> C.CDLL:
         "sps_penalty_apply_noalloc": (I, [I, C.POINTER(C.c_int), C.POINTER(D), C.POINTER(D), D, P, P, P]),
         "sps_level_matrix": (I, [P, I, P, C.POINTER(C.c_int64), I, P]),
         "sps_plan_device_bytes": (I, [P, C.POINTER(C.c_int64)]),
+        "sps_solve_batch_shape": (I, [C.POINTER(P), I, C.POINTER(P), I, D, C.POINTER(sps_batch_shape),
+                                      C.POINTER(sps_result), C.POINTER(sps_batch_shape), P]),
+        "sps_tune_batch": (I, [C.POINTER(P), I, C.POINTER(P), I, D, C.POINTER(sps_batch_shape), P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -196,6 +203,38 @@ def sps_solve_batch(plans, coefs, tol, stream=None, check=True) -> list:
     if check:
         _check(code, "sps_solve_batch")
     return list(res)
+
+
+def _batch_args(plans, coefs):
+    n = len(plans)
+    ph = (C.c_void_p * n)(*[p.value if isinstance(p, C.c_void_p) else p for p in plans])
+    bufs = [_buf(c) for c in coefs]
+    mems = {m for _, m in bufs}
+    if len(mems) != 1:
+        raise ValueError("all coefficient buffers must live in the same memory")
+    ch = (C.c_void_p * n)(*[b[0].value for b in bufs])
+    return n, ph, ch, mems.pop()
+
+
+def sps_solve_batch_shape(plans, coefs, tol, cluster=None, big=-1, stream=None, check=True) -> tuple:
+    """Batched solve with an explicit shape (cluster None: the tuned or default
+    shape); returns (results, shape that ran)."""
+    n, ph, ch, mem = _batch_args(plans, coefs)
+    res = (sps_result * n)()
+    used = sps_batch_shape()
+    shp = C.byref(sps_batch_shape(cluster, big, 0.0)) if cluster is not None else None
+    code = lib().sps_solve_batch_shape(ph, n, ch, mem, tol, shp, res, C.byref(used), _stream(stream))
+    if check:
+        _check(code, "sps_solve_batch_shape")
+    return list(res), (used.cluster, used.big)
+
+
+def sps_tune_batch(plans, coefs, tol, stream=None) -> tuple:
+    """Autotune the batched solver for these problems: (cluster, big, predicted ms)."""
+    n, ph, ch, mem = _batch_args(plans, coefs)
+    best = sps_batch_shape()
+    _check(lib().sps_tune_batch(ph, n, ch, mem, tol, C.byref(best), _stream(stream)), "sps_tune_batch")
+    return best.cluster, best.big, best.predicted_ms
 
 
 SPS_NOALLOC_MAX_COEF = 262144

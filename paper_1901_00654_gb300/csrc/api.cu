@@ -1050,8 +1050,8 @@ int sps_solve(sps_plan* pl, double* coef, int mem, double tol, sps_result* res_o
   return res.status;
 }
 
-int sps_solve_batch(sps_plan* const* plans, int count, double* const* coefs, int mem, double tol,
-                    sps_result* results, void* stream) {
+namespace {
+int check_batch(sps_plan* const* plans, int count, double* const* coefs, int mem, double tol) {
   if (!plans || !coefs || count < 1 || !(tol > 0.0) || (mem != SPS_MEM_HOST && mem != SPS_MEM_DEVICE)) {
     set_error("invalid batch arguments");
     return SPS_EINVAL;
@@ -1069,7 +1069,31 @@ int sps_solve_batch(sps_plan* const* plans, int count, double* const* coefs, int
       return SPS_EINVAL;
     }
   }
-  return solve_batch(plans, count, coefs, mem, tol, results, as_stream(stream));
+  return SPS_OK;
+}
+}  // namespace
+
+int sps_solve_batch(sps_plan* const* plans, int count, double* const* coefs, int mem, double tol,
+                    sps_result* results, void* stream) {
+  SPS_TRY(check_batch(plans, count, coefs, mem, tol));
+  return solve_batch(plans, count, coefs, mem, tol, nullptr, results, nullptr, as_stream(stream));
+}
+
+int sps_solve_batch_shape(sps_plan* const* plans, int count, double* const* coefs, int mem, double tol,
+                          const sps_batch_shape* shape, sps_result* results, sps_batch_shape* used, void* stream) {
+  SPS_TRY(check_batch(plans, count, coefs, mem, tol));
+  if (shape && ((shape->cluster != 1 && shape->cluster != 2 && shape->cluster != 4 && shape->cluster != 8) ||
+                shape->big < -1)) {
+    set_error("batch shape: cluster must be 1, 2, 4 or 8 and big >= -1");
+    return SPS_EINVAL;
+  }
+  return solve_batch(plans, count, coefs, mem, tol, shape, results, used, as_stream(stream));
+}
+
+int sps_tune_batch(sps_plan* const* plans, int count, double* const* coefs, int mem, double tol,
+                   sps_batch_shape* best, void* stream) {
+  SPS_TRY(check_batch(plans, count, coefs, mem, tol));
+  return tune_batch(plans, count, coefs, mem, tol, best, as_stream(stream));
 }
 
 int sps_coef_count(const sps_plan* pl, int level, int64_t* K) {

@@ -16,8 +16,10 @@
 
 #include <algorithm>
 #include <cmath>
-#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <queue>
 #include <vector>
 
 #include "sps_internal.h"
@@ -588,14 +590,62 @@ __global__ void __launch_bounds__(BT, 1) k_batch_solve(const BatchProblem* __res
 
 }  // namespace
 
-// Host side of sps_solve_batch: descriptors, cost order, graph launch.
-int solve_batch(sps_plan* const* plans, int count, double* const* coefs, int mem, double tol, sps_result* res,
-                cudaStream_t st) {
-  std::vector<BatchProblem> hp(count);
-  std::vector<double> cost(count);
+// ---------------------------------------------------------------- host side
+
+namespace {
+
+// Batch signature (count and every problem's P, K, n) -> the autotuner's shape.
+std::mutex g_tune_mu;
+std::map<unsigned long long, sps_batch_shape> g_tuned;
+
+unsigned long long batch_signature(sps_plan* const* plans, int count) {
+  unsigned long long h = 1469598103934665603ull ^ (unsigned long long)count;
+  for (int i = 0; i < count; ++i) {
+    const unsigned long long v[3] = {(unsigned long long)plans[i]->P,
+                                     (unsigned long long)plans[i]->lev[plans[i]->G - 1].geom.K,
+                                     (unsigned long long)plans[i]->n};
+    for (unsigned long long x : v) {
+      h ^= x + 0x9E3779B97F4A7C15ull + (h << 6) + (h >> 2);
+      h *= 1099511628211ull;
+    }
+  }
+  return h;
+}
+
+// CTAs of the persistent launch for cluster size C (C = 1: no cluster), or 0
+// when such clusters cannot be resident.
+int batch_grid(int C, int count, int sms) {
+  if (C == 1) return std::min(count, sms);
+  cudaLaunchConfig_t oc = {};
+  oc.gridDim = dim3(((sms + C - 1) / C) * C);
+  oc.blockDim = dim3(BT);
+  cudaLaunchAttribute oa;
+  oa.id = cudaLaunchAttributeClusterDimension;
+  oa.val.clusterDim.x = C;
+  oa.val.clusterDim.y = 1;
+  oa.val.clusterDim.z = 1;
+  oc.attrs = &oa;
+  oc.numAttrs = 1;
+  int clusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&clusters, k_batch_solve, &oc) != cudaSuccess || clusters < 1) {
+    cudaGetLastError();
+    return 0;
+  }
+  return clusters * C;
+}
+
+struct BatchHost {
+  std::vector<BatchProblem> hp;
+  std::vector<double> cost;
+  std::vector<int> order;   // problems by decreasing cost
+};
+
+void build_descriptors(sps_plan* const* plans, int count, double tol, BatchHost& bh) {
+  bh.hp.assign(count, BatchProblem());
+  bh.cost.assign(count, 0.0);
   for (int i = 0; i < count; ++i) {
     sps_plan* pl = plans[i];
-    BatchProblem& b = hp[i];
+    BatchProblem& b = bh.hp[i];
     std::memset(&b, 0, sizeof(b));
     b.P = pl->P;
     b.G = pl->G;
@@ -639,12 +689,28 @@ int solve_batch(sps_plan* const* plans, int count, double* const* coefs, int mem
       bl.S = L.S;
       bl.omega = (float)L.omega;
     }
-    cost[i] = (double)pl->n * pl->G * (double)(1 << (2 * pl->P)) + (double)pl->lev[pl->G - 1].geom.K * 50.0;
+    bh.cost[i] = (double)pl->n * pl->G * (double)(1 << (2 * pl->P)) + (double)pl->lev[pl->G - 1].geom.K * 50.0;
   }
-  std::vector<int> order(count);
-  for (int i = 0; i < count; ++i) order[i] = i;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
-  // one allocation per call holds descriptors, order, queue and results
+  bh.order.resize(count);
+  for (int i = 0; i < count; ++i) bh.order[i] = i;
+  std::stable_sort(bh.order.begin(), bh.order.end(), [&](int a, int b) { return bh.cost[a] > bh.cost[b]; });
+}
+
+// The default split: problems whose cost exceeds a balanced share of the
+// batch per CTA would bound the batch's time if one CTA solved them.
+int default_big(const BatchHost& bh, int grid) {
+  double total = 0.0;
+  for (double c : bh.cost) total += c;
+  const double share = total / std::max(grid, 1);
+  int big = 0;
+  while (big < (int)bh.order.size() && bh.cost[bh.order[big]] > share) ++big;
+  return big;
+}
+
+// One persistent launch of the whole batch with cluster size C and `big`
+// problems solved by clusters; per-problem outputs (status, times) in out.
+int run_batch(sps_plan* const* plans, int count, const BatchHost& bh, int C, int big, int grid,
+              std::vector<BatchOut>& out, cudaStream_t st) {
   const size_t sz_p = sizeof(BatchProblem) * count, sz_o = sizeof(int) * count, sz_r = sizeof(BatchOut) * count;
   const size_t off_o = (sz_p + 255) & ~(size_t)255, off_q = (off_o + sz_o + 255) & ~(size_t)255,
                off_r = off_q + 256, total = off_r + sz_r;
@@ -658,50 +724,8 @@ int solve_batch(sps_plan* const* plans, int count, double* const* coefs, int mem
     char* p;
     ~Free() { cudaFree(p); }
   } guard{dev};
-  SPS_CUDA(cudaMemcpyAsync(dev, hp.data(), sz_p, cudaMemcpyHostToDevice, st));
-  SPS_CUDA(cudaMemcpyAsync(dev + off_o, order.data(), sz_o, cudaMemcpyHostToDevice, st));
-  int sms = 0, devid = 0;
-  SPS_CUDA(cudaGetDevice(&devid));
-  SPS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, devid));
-  // Problems whose cost exceeds a balanced share of the whole batch per CTA
-  // would bound the batch's time if solved by one CTA: thread-block clusters
-  // of C CTAs (C = 2 unless SPS_BATCH_CLUSTER says 1, 4 or 8) solve those
-  // together first, then every CTA takes the rest alone.  Each phase of a
-  // solve is short, so cluster barriers soon cost more than the extra CTAs
-  // gain: on the 512-problem batch C = 2 gave the shortest batch time.
-  int C = 2;
-  if (const char* e = getenv("SPS_BATCH_CLUSTER")) {
-    const int c = atoi(e);
-    if (c == 1 || c == 2 || c == 4 || c == 8) C = c;
-  }
-  int grid = std::min(count, sms);
-  if (C > 1) {
-    cudaLaunchConfig_t oc = {};
-    oc.gridDim = dim3(((sms + C - 1) / C) * C);
-    oc.blockDim = dim3(BT);
-    cudaLaunchAttribute oa;
-    oa.id = cudaLaunchAttributeClusterDimension;
-    oa.val.clusterDim.x = C;
-    oa.val.clusterDim.y = 1;
-    oa.val.clusterDim.z = 1;
-    oc.attrs = &oa;
-    oc.numAttrs = 1;
-    int clusters = 0;
-    cudaError_t oe = cudaOccupancyMaxActiveClusters(&clusters, k_batch_solve, &oc);
-    if (oe != cudaSuccess || clusters < 1) {
-      cudaGetLastError();
-      C = 1;
-    } else {
-      grid = clusters * C;
-    }
-  }
-  int nbig = 0;
-  if (C > 1) {
-    double total = 0.0;
-    for (int i = 0; i < count; ++i) total += cost[i];
-    const double share = total / grid;
-    while (nbig < count && cost[order[nbig]] > share) ++nbig;
-  }
+  SPS_CUDA(cudaMemcpyAsync(dev, bh.hp.data(), sz_p, cudaMemcpyHostToDevice, st));
+  SPS_CUDA(cudaMemcpyAsync(dev + off_o, bh.order.data(), sz_o, cudaMemcpyHostToDevice, st));
   // capture: reset the queue, then the persistent kernel
   cudaGraph_t graph;
   cudaGraphExec_t exec;
@@ -726,7 +750,7 @@ int solve_batch(sps_plan* const* plans, int count, double* const* coefs, int mem
     const int* a1 = (const int*)(dev + off_o);
     int* a3 = (int*)(dev + off_q);
     BatchOut* a4 = (BatchOut*)(dev + off_r);
-    const cudaError_t le = cudaLaunchKernelEx(&cfg, k_batch_solve, a0, a1, count, nbig, a3, a4, C);
+    const cudaError_t le = cudaLaunchKernelEx(&cfg, k_batch_solve, a0, a1, count, C > 1 ? big : 0, a3, a4, C);
     if (le != cudaSuccess) {
       cudaGraph_t dummy;
       cudaStreamEndCapture(cs, &dummy);
@@ -744,14 +768,56 @@ int solve_batch(sps_plan* const* plans, int count, double* const* coefs, int mem
   cudaGraphExecDestroy(exec);
   cudaGraphDestroy(graph);
   cudaStreamDestroy(cs);
-  std::vector<BatchOut> out(count);
+  out.resize(count);
   SPS_CUDA(cudaMemcpy(out.data(), dev + off_r, sz_r, cudaMemcpyDeviceToHost));
-  int worst = SPS_OK;
+  return SPS_OK;
+}
+
+// Makespan of the persistent queues with measured per-problem times: `grid`
+// CTAs as grid / C teams take the `big` costliest problems (times tc); a team
+// that finds that queue empty splits into C single CTAs, which take the rest
+// in cost order (times t1).  C = 1: single CTAs throughout.
+double simulate_batch(const std::vector<int>& order, const std::vector<double>& t1, const std::vector<double>& tc,
+                      int C, int big, int grid) {
+  using Ev = std::pair<double, int>;   // (time free, team size)
+  std::priority_queue<Ev, std::vector<Ev>, std::greater<Ev>> q;
+  const int teams = C > 1 ? grid / C : grid;
+  for (int t = 0; t < teams; ++t) q.push({0.0, C > 1 ? C : 1});
+  int next_big = 0, next = C > 1 ? big : 0;
+  const int n = (int)order.size();
+  double makespan = 0.0;
+  while (!q.empty()) {
+    const Ev e = q.top();
+    q.pop();
+    if (e.second > 1) {
+      if (next_big < big) {
+        const double f = e.first + tc[order[next_big++]];
+        makespan = std::max(makespan, f);
+        q.push({f, e.second});
+      } else {
+        for (int k = 0; k < e.second; ++k) q.push({e.first, 1});
+      }
+    } else if (next < n) {
+      const double f = e.first + t1[order[next++]];
+      makespan = std::max(makespan, f);
+      q.push({f, 1});
+    }
+  }
+  return makespan;
+}
+
+void fill_results(sps_plan* const* plans, int count, double* const* coefs, int mem, const std::vector<BatchOut>& out,
+                  sps_result* res, int* worst, cudaStream_t st, int* rc) {
+  *worst = SPS_OK;
   for (int i = 0; i < count; ++i) {
     sps_plan* pl = plans[i];
     const long long K = pl->lev[pl->G - 1].geom.K;
-    SPS_CUDA(cudaMemcpyAsync(coefs[i], pl->x, sizeof(double) * K,
-                             mem == SPS_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+    const cudaError_t e = cudaMemcpyAsync(coefs[i], pl->x, sizeof(double) * K,
+                                          mem == SPS_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) {
+      *rc = cuda_fail(e, "copy of batch coefficients");
+      return;
+    }
     if (res) {
       sps_result& r = res[i];
       std::memset(&r, 0, sizeof(r));
@@ -762,11 +828,92 @@ int solve_batch(sps_plan* const* plans, int count, double* const* coefs, int mem
       r.fp64_applies = out[i].fp64_applies;
       r.solve_ms = out[i].ms;
     }
-    if (out[i].status != SPS_OK && worst == SPS_OK) worst = out[i].status;
+    if (out[i].status != SPS_OK && *worst == SPS_OK) *worst = out[i].status;
   }
+}
+
+}  // namespace
+
+// Host side of sps_solve_batch: descriptors, cost order, shape, graph launch.
+int solve_batch(sps_plan* const* plans, int count, double* const* coefs, int mem, double tol,
+                const sps_batch_shape* shape, sps_result* res, sps_batch_shape* used, cudaStream_t st) {
+  BatchHost bh;
+  build_descriptors(plans, count, tol, bh);
+  int sms = 0, devid = 0;
+  SPS_CUDA(cudaGetDevice(&devid));
+  SPS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, devid));
+  sps_batch_shape sh = {2, -1, 0.0};   // clusters of two CTAs for the costliest problems
+  if (shape) {
+    sh = *shape;
+  } else {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tuned.find(batch_signature(plans, count));
+    if (it != g_tuned.end()) sh = it->second;
+  }
+  int C = sh.cluster;
+  int grid = batch_grid(C, count, sms);
+  if (grid == 0) {   // such clusters cannot be resident: one CTA per problem
+    C = 1;
+    grid = batch_grid(1, count, sms);
+  }
+  const int big = C == 1 ? 0 : (sh.big < 0 ? default_big(bh, grid) : std::min(sh.big, count));
+  std::vector<BatchOut> out;
+  SPS_TRY(run_batch(plans, count, bh, C, big, grid, out, st));
+  if (used) {
+    used->cluster = C;
+    used->big = big;
+    used->predicted_ms = sh.predicted_ms;
+  }
+  int worst = SPS_OK, rc = SPS_OK;
+  fill_results(plans, count, coefs, mem, out, res, &worst, st, &rc);
+  if (rc != SPS_OK) return rc;
   SPS_CUDA(cudaStreamSynchronize(st));
   if (worst != SPS_OK) set_error("at least one problem of the batch did not converge");
   return worst;
+}
+
+// The autotuner: solve the batch once per cluster size C in {1, 2, 4, 8} with
+// every problem on a team of C CTAs, keep the measured time of every problem
+// for every C, then choose the cluster size and the number of problems solved
+// by clusters whose simulated batch time is the shortest.
+int tune_batch(sps_plan* const* plans, int count, double* const* coefs, int mem, double tol, sps_batch_shape* best,
+               cudaStream_t st) {
+  BatchHost bh;
+  build_descriptors(plans, count, tol, bh);
+  int sms = 0, devid = 0;
+  SPS_CUDA(cudaGetDevice(&devid));
+  SPS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, devid));
+  const int cands[4] = {1, 2, 4, 8};
+  std::vector<double> times[4];
+  int grids[4] = {0, 0, 0, 0};
+  std::vector<BatchOut> out;
+  for (int c = 0; c < 4; ++c) {
+    const int C = cands[c];
+    grids[c] = batch_grid(C, count, sms);
+    if (grids[c] == 0) continue;
+    SPS_TRY(run_batch(plans, count, bh, C, count, grids[c], out, st));
+    times[c].resize(count);
+    for (int i = 0; i < count; ++i) times[c][i] = out[i].ms;
+  }
+  sps_batch_shape pick = {1, 0, simulate_batch(bh.order, times[0], times[0], 1, 0, grids[0])};
+  for (int c = 1; c < 4; ++c) {
+    if (grids[c] == 0) continue;
+    for (int big = 1; big <= count; ++big) {
+      const double m = simulate_batch(bh.order, times[0], times[c], cands[c], big, grids[c]);
+      if (m < pick.predicted_ms) pick = {cands[c], big, m};
+    }
+  }
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tuned[batch_signature(plans, count)] = pick;
+  }
+  if (best) *best = pick;
+  // leave the coefficients of the last tuning run in coefs (a valid solve)
+  int worst = SPS_OK, rc = SPS_OK;
+  fill_results(plans, count, coefs, mem, out, nullptr, &worst, st, &rc);
+  if (rc != SPS_OK) return rc;
+  SPS_CUDA(cudaStreamSynchronize(st));
+  return SPS_OK;
 }
 
 }  // namespace sps

@@ -220,6 +220,84 @@ k_point(const WorkItem* __restrict__ items, const int* __restrict__ run_begin,
 #pragma unroll
     for (int k = 0; k < NR; ++k) accr[k] = T(0);
 
+    if constexpr (VREG && MODE == PT_APPLY && R == 2 && !PRE) {
+      // FP32 apply with 16 sums per lane, two points per step: the two points'
+      // basis values, gathers and group reductions are independent chains that
+      // the scheduler interleaves (one point at a time is latency bound).
+      auto basis = [&](int i, T (&bv)[P][4], T& fixw) {
+        fixw = T(1);
+        if (SHARED_BASIS) {
+          const T t = fma(T(xsh[sdim * npts + (i - pbeg)]), sinv, -stsh);
+          const T val = fma(fma(fma(sc3, t, sc2), t, sc1), t, sc0);
+          fixw = __shfl_sync(gmask, val, mfix[0], TPP) * __shfl_sync(gmask, val, 4 + mfix[F > 1 ? 1 : 0], TPP);
+#pragma unroll
+          for (int m = 0; m < 4; ++m) {
+            bv[P - 2][m] = __shfl_sync(gmask, val, 8 + m, TPP);
+            bv[P - 1][m] = __shfl_sync(gmask, val, 12 + m, TPP);
+          }
+        } else {
+#pragma unroll
+          for (int p = 0; p < P; ++p) {
+            const T t = fma(T(xsh[p * npts + (i - pbeg)]), inv[p], -tsh[p]);
+            if (ONEPIECE && p < F) {
+              const int q = ONEPIECE ? p : 0;
+              fixw *= fma(fma(fma(pc3[q], t, pc2[q]), t, pc1[q]), t, pc0[q]);
+            } else if (p >= P - 2) {
+              cubic_basis(t, bv[p]);
+            } else {
+              T b4[4];
+              cubic_basis(t, b4);
+              const int m = mfix[p < F ? p : 0];
+              fixw *= m == 0 ? b4[0] : m == 1 ? b4[1] : m == 2 ? b4[2] : b4[3];
+            }
+          }
+        }
+      };
+      auto gather = [&](const T (&bv)[P][4]) -> T {
+        T g = T(0);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          T s1 = T(0);
+#pragma unroll
+          for (int d = 0; d < 4; ++d) s1 = fma(bv[P - 1][d], vr[VREG ? a * 4 + d : 0], s1);
+          g = fma(bv[P - 2][a], s1, g);
+        }
+        return g;
+      };
+      int i = i0;
+      for (; i + 1 < i1; i += 2) {
+        T bA[P][4], bB[P][4], fA, fB;
+        basis(i, bA, fA);
+        basis(i + 1, bB, fB);
+        T gA = gather(bA) * fA, gB = gather(bB) * fB;
+#pragma unroll
+        for (int o = TPP / 2; o >= 1; o >>= 1) {
+          gA += __shfl_xor_sync(gmask, gA, o, TPP);
+          gB += __shfl_xor_sync(gmask, gB, o, TPP);
+        }
+        const T wA = gA * fA, wB = gB * fB;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const T tA = wA * bA[P - 2][a], tB = wB * bB[P - 2][a];
+#pragma unroll
+          for (int d = 0; d < 4; ++d) accr[a * 4 + d] = fma(tB, bB[P - 1][d], fma(tA, bA[P - 1][d], accr[a * 4 + d]));
+        }
+      }
+      if (i < i1) {
+        T bA[P][4], fA;
+        basis(i, bA, fA);
+        T gA = gather(bA) * fA;
+#pragma unroll
+        for (int o = TPP / 2; o >= 1; o >>= 1) gA += __shfl_xor_sync(gmask, gA, o, TPP);
+        const T wA = gA * fA;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const T tA = wA * bA[P - 2][a];
+#pragma unroll
+          for (int d = 0; d < 4; ++d) accr[a * 4 + d] = fma(tA, bA[P - 1][d], accr[a * 4 + d]);
+        }
+      }
+    } else
     for (int i = i0; i < i1; ++i) {
       if constexpr (PRE == 2 && P == 3 && R == 2 && MODE == PT_APPLY) {
         // products b2[b] b3[d] precomputed: 16 multiply-adds each way per lane

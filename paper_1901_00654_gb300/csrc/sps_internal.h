@@ -270,8 +270,10 @@ int pcg_update_xr(sps_plan* pl, long long n, int rz_slot, cudaStream_t st);
 int pcg_update_p(sps_plan* pl, long long n, int num_slot, int den_slot, int flexible, cudaStream_t st);
 
 // ---- batch.cu ----
-int solve_batch(sps_plan* const* plans, int count, double* const* coefs, int mem, double tol, sps_result* res,
-                cudaStream_t st);
+int solve_batch(sps_plan* const* plans, int count, double* const* coefs, int mem, double tol,
+                const sps_batch_shape* shape, sps_result* res, sps_batch_shape* used, cudaStream_t st);
+int tune_batch(sps_plan* const* plans, int count, double* const* coefs, int mem, double tol, sps_batch_shape* best,
+               cudaStream_t st);
 
 // ---- solver (api.cu) ----
 template <typename T>

@@ -15,11 +15,10 @@ def _problems(count, seed=3, n_hi=2e4):
     return W.batched(seed=seed, count=count, n_lo=1e3, n_hi=n_hi)
 
 
-@pytest.fixture(params=["1", "2", "4", "8"])
-def cluster(request, monkeypatch):
-    """Thread-block cluster size of the batched kernel (read at every call)."""
-    monkeypatch.setenv("SPS_BATCH_CLUSTER", request.param)
-    return int(request.param)
+@pytest.fixture(params=[1, 2, 4, 8])
+def cluster(request):
+    """Thread-block cluster size of the batched kernel's launch shape."""
+    return request.param
 
 
 def test_batch_matches_oracle_residual_and_single_solves(cluster):
@@ -32,7 +31,8 @@ def test_batch_matches_oracle_residual_and_single_solves(cluster):
             pl.set_points(pr.x, pr.y)
             plans.append(pl)
         coefs = [np.zeros(pl.K) for pl in plans]
-        res = B.sps_solve_batch([pl.h for pl in plans], coefs, tol)
+        res, used = B.sps_solve_batch_shape([pl.h for pl in plans], coefs, tol, cluster=cluster)
+        assert used[0] == cluster
         for pr, pl, c, r in zip(probs, plans, coefs, res):
             assert r.status == B.SPS_OK and r.rel_res_true <= tol
             A, b, _, _ = spline.system(pr.x, pr.y, pr.lo, pr.hi, pr.intervals, 3, pr.lam)
@@ -52,7 +52,7 @@ def test_batch_single_problem(cluster):
     with B.Plan(pr.P, pr.intervals, pr.levels, pr.lam, pr.lo, pr.hi, precision=B.SPS_PREC_MIXED) as pl:
         pl.set_points(pr.x, pr.y)
         c = np.zeros(pl.K)
-        (r,) = B.sps_solve_batch([pl.h], [c], 1e-8)
+        (r,), _ = B.sps_solve_batch_shape([pl.h], [c], 1e-8, cluster=cluster)
         assert r.status == B.SPS_OK and r.rel_res_true <= 1e-8
         A, b, _, _ = spline.system(pr.x, pr.y, pr.lo, pr.hi, pr.intervals, 3, pr.lam)
         assert np.linalg.norm(b - A @ c) / np.linalg.norm(b) <= 1.05e-8
@@ -92,3 +92,35 @@ def test_batch_rejects_p4():
         with pytest.raises(B.SpsError) as e:
             B.sps_solve_batch([pl.h], [np.zeros(pl.K)], 1e-8)
         assert e.value.code == B.SPS_EINVAL
+
+
+def test_batch_autotuner_picks_a_measured_shape():
+    """sps_tune_batch measures every cluster size and picks the shape with the
+    shortest simulated batch time; later sps_solve_batch calls on the same
+    problems use it, converge, and take no longer than the simulation said
+    (within launch and timing noise)."""
+    import time
+    probs = _problems(48, seed=13, n_hi=5e4)
+    tol = 1e-8
+    plans = []
+    try:
+        for pr in probs:
+            pl = B.Plan(pr.P, pr.intervals, pr.levels, pr.lam, pr.lo, pr.hi, precision=B.SPS_PREC_MIXED)
+            pl.set_points(pr.x, pr.y)
+            plans.append(pl)
+        hs = [pl.h for pl in plans]
+        coefs = [np.zeros(pl.K) for pl in plans]
+        cluster, big, predicted = B.sps_tune_batch(hs, coefs, tol)
+        assert cluster in (1, 2, 4, 8) and 0 <= big <= len(probs) and predicted > 0
+        t0 = time.perf_counter()
+        res = B.sps_solve_batch(hs, coefs, tol)
+        wall = (time.perf_counter() - t0) * 1e3
+        assert all(r.status == B.SPS_OK and r.rel_res_true <= tol for r in res)
+        _, used = B.sps_solve_batch_shape(hs, coefs, tol)          # no shape given: the tuned one
+        assert used == (cluster, big if cluster > 1 else 0)
+        print("batch autotuner: cluster %d, %d problems on clusters, simulated %.1f ms, measured %.1f ms"
+              % (cluster, big, predicted, wall))
+        assert wall < 3.0 * predicted + 50.0
+    finally:
+        for pl in plans:
+            pl.close()
