@@ -23,23 +23,38 @@ import numpy as np
 from . import binding as B
 
 
-def estimate_bytes(P: int, intervals, levels: int, n: int, itemsize: int = 8) -> int:
-    """Device memory of one plan: points (coordinates, response, keys,
-    permutation, sort scratch, runs per level) plus about 30 coefficient
-    vectors per level and the dense coarse inverse."""
-    K = 0
+def estimate_bytes(P: int, intervals, levels: int, n: int, itemsize: int = 8,
+                   precision: int = B.SPS_PREC_MIXED) -> int:
+    """Upper bound of the device memory of one plan after sps_set_points:
+      * points: sorted coordinates (input type and an FP32 copy), responses,
+        keys and permutation with their sort scratch, run lists per level;
+      * about 30 coefficient vectors per level (FP64 and FP32 copies, the
+        penalty and transfer temporaries, the PCG vectors);
+      * the dense coarse solver: A_1, its inverse Cholesky factor and its
+        transpose, and the scaled working copy (4 K_1^2 doubles);
+      * the assembled stencils of the levels strictly between the coarsest
+        and the finest, (2q+1)^P entries per coefficient where that fits the
+        library's 8 GB per level (FP64; mixed plans hold an FP64 and an FP32
+        copy while assembling);
+      * FP64 plans: the precomputed basis values (and, for P = 3, products)
+        of every point on every level above the coarsest."""
+    Ks = []
     for g in range(levels):
         k = 1
         for N in intervals:
             k *= (N >> g) + 3
-        K += k
-    k1 = 1
-    for N in intervals:
-        k1 *= (N >> (levels - 1)) + 3
-    points = n * (P * itemsize + 8 + 16 + 8 + 12 * levels)
-    vectors = K * 8 * 30
-    coarse = k1 * k1 * 12
-    return int(points + vectors + coarse + (64 << 20))
+        Ks.append(k)                        # Ks[0] is the finest level
+    K1 = Ks[-1]
+    S = 7 ** P
+    points = n * (P * itemsize + P * 4 + 8 + 16 + 8 + 12 * levels)
+    vectors = sum(Ks) * 8 * 30
+    coarse = K1 * K1 * 8 * 4
+    stencil_bytes = 12 if precision == B.SPS_PREC_MIXED else 8
+    stencils = sum(S * k * stencil_bytes for k in Ks[1:-1] if S * k * 8 <= 8e9)
+    pre = 0
+    if precision == B.SPS_PREC_FP64:
+        pre = (levels - 1) * n * (4 * P + (20 if P == 3 else 0)) * 8
+    return int(points + vectors + coarse + stencils + pre + (64 << 20))
 
 
 @dataclass
@@ -167,7 +182,8 @@ class Server:
                 while waiting:
                     i = waiting[0]
                     pr = trace[i].problem
-                    est = estimate_bytes(pr.P, pr.intervals, pr.levels, pr.n, pr.x.dtype.itemsize)
+                    est = estimate_bytes(pr.P, pr.intervals, pr.levels, pr.n, pr.x.dtype.itemsize,
+                                         self.precision)
                     if self._in_flight >= self.slots or (self._used + est > self.budget and self._in_flight > 0):
                         break
                     waiting.popleft()
