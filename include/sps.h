@@ -134,7 +134,9 @@ typedef struct sps_result {
     int    iterations;     /* outer CG iterations (operator applies on level G) */
     double rel_res;        /* |r| / |Phi'y| of the recursive residual at exit */
     double rel_res_true;   /* |Phi'y - A alpha| / |Phi'y| recomputed in FP64 at exit */
-    int    fp64_applies;   /* FP64 applies on level G (MIXED: residual replacements) */
+    int    fp64_applies;   /* FP64 applies on level G (MIXED: residual replacements, plus
+                              one per iteration after a fallback to the FP64 outer
+                              operator, which an FP32 breakdown triggers) */
     double solve_ms;       /* wall time of sps_solve (host clock) */
 } sps_result;
 

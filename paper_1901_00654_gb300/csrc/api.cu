@@ -502,6 +502,11 @@ int solve_fp64(sps_plan* pl, double tol, sps_result* res, bool warm, cudaStream_
 // Flexible PCG (Polak-Ribiere beta, Notay 2000) in FP64 with the FP32 V-cycle
 // and FP32 point operator; the FP64 residual b - A alpha is recomputed when
 // the recursive residual has dropped by replace_ratio (reliable updates).
+// When the FP32 outer operator breaks the iteration down (p'A p <= 0 or a
+// non-finite step: the system is too ill-conditioned for FP32 to resolve), the
+// solve restarts from the current iterate with the FP64 residual and goes on
+// with the FP64 outer operator (the V-cycle stays FP32); a breakdown after
+// that is reported.
 int solve_mixed(sps_plan* pl, double tol, sps_result* res, bool warm, cudaStream_t st) {
   const int G = pl->G;
   Level& LG = pl->lev[G - 1];
@@ -512,6 +517,7 @@ int solve_mixed(sps_plan* pl, double tol, sps_result* res, bool warm, cudaStream
   int it = 0, status = SPS_OK;
   double rel = 1.0, rlast = 0.0;
   const double ratio = pl->opt.replace_ratio > 0 ? pl->opt.replace_ratio : 1e-2;
+  bool outer64 = false;   // FP64 outer operator after an FP32 breakdown
   SPS_CUDA(cudaMemsetAsync(pl->scal, 0, sizeof(double) * NSCAL, st));
   if (warm) {
     SPS_TRY(apply_level<double>(pl, G, pl->x, pl->v, st));
@@ -531,11 +537,15 @@ int solve_mixed(sps_plan* pl, double tol, sps_result* res, bool warm, cudaStream
     SPS_TRY(vcycle_into<float>(pl, LG.f.b, a32, s));
     return vec_cast_f2d(pl->z, a32, K, s);
   };
-  // v = A32 p; w = r'z / p'v; alpha += w p; r -= w v
+  // v = A32 p (A64 p after a breakdown); w = r'z / p'v; alpha += w p; r -= w v
   auto half_apply = [&](cudaStream_t s) -> int {
-    SPS_TRY(vec_cast_d2f(pl->p32, pl->p, K, s));
-    SPS_TRY(apply_level<float>(pl, G, pl->p32, v32, s));            // FP32 operator
-    SPS_TRY(vec_cast_f2d(pl->v, v32, K, s));
+    if (outer64) {
+      SPS_TRY(apply_level<double>(pl, G, pl->p, pl->v, s));
+    } else {
+      SPS_TRY(vec_cast_d2f(pl->p32, pl->p, K, s));
+      SPS_TRY(apply_level<float>(pl, G, pl->p32, v32, s));          // FP32 operator
+      SPS_TRY(vec_cast_f2d(pl->v, v32, K, s));
+    }
     SPS_TRY(dot(pl, pl->p, pl->v, K, S_PV, s));
     SPS_CUDA(cudaMemcpyAsync(pl->rprev, pl->r, sizeof(double) * K, cudaMemcpyDeviceToDevice, s));
     SPS_TRY(pcg_update_xr(pl, K, S_RZ_A, s));
@@ -563,12 +573,29 @@ int solve_mixed(sps_plan* pl, double tol, sps_result* res, bool warm, cudaStream
       SPS_CUDA(cudaStreamSynchronize(st));
       restarted = false;
     } else {
-      SPS_TRY(run_iteration(pl, 1, body, st));
+      SPS_TRY(run_iteration(pl, outer64 ? 2 : 1, body, st));
     }
     ++it;
+    if (outer64) res->fp64_applies++;
     if (pl->host_scal[S_FLAG] != 0.0) {
-      status = SPS_EBREAKDOWN;
-      break;
+      if (outer64) {
+        status = SPS_EBREAKDOWN;
+        break;
+      }
+      // the step was not taken (x, r unchanged): FP64 residual, V-cycle, new direction
+      outer64 = true;
+      SPS_CUDA(cudaMemsetAsync(pl->scal, 0, sizeof(double) * NSCAL, st));
+      SPS_TRY(apply_level<double>(pl, G, pl->x, pl->v, st));
+      SPS_TRY(vec_residual(pl->r, pl->rhs, pl->v, K, pl->scal, S_RR, pl, st));
+      res->fp64_applies++;
+      SPS_TRY(precondition(st));
+      SPS_CUDA(cudaMemcpyAsync(pl->p, pl->z, sizeof(double) * K, cudaMemcpyDeviceToDevice, st));
+      SPS_TRY(dot(pl, pl->r, pl->z, K, S_RZ_A, st));
+      SPS_TRY(read_scalars(pl, st));
+      rlast = std::sqrt(pl->host_scal[S_RR]);
+      rel = rlast / nb;
+      restarted = true;
+      continue;
     }
     double rn = std::sqrt(pl->host_scal[S_RR]);
     rel = rn / nb;
@@ -586,8 +613,28 @@ int solve_mixed(sps_plan* pl, double tol, sps_result* res, bool warm, cudaStream
       SPS_CUDA(cudaStreamSynchronize(st));
       ++it;
       if (pl->host_scal[S_FLAG] != 0.0) {
-        status = SPS_EBREAKDOWN;
-        break;
+        if (outer64) {
+          status = SPS_EBREAKDOWN;
+          break;
+        }
+        outer64 = true;   // handled at the top of the loop on the next breakdown check
+        SPS_CUDA(cudaMemsetAsync(pl->scal + S_FLAG, 0, sizeof(double), st));
+        SPS_CUDA(cudaStreamSynchronize(st));
+        pl->host_scal[S_FLAG] = 0.0;
+        restarted = false;
+        // restart as above: FP64 residual from the (unchanged) iterate
+        SPS_CUDA(cudaMemsetAsync(pl->scal, 0, sizeof(double) * NSCAL, st));
+        SPS_TRY(apply_level<double>(pl, G, pl->x, pl->v, st));
+        SPS_TRY(vec_residual(pl->r, pl->rhs, pl->v, K, pl->scal, S_RR, pl, st));
+        res->fp64_applies++;
+        SPS_TRY(precondition(st));
+        SPS_CUDA(cudaMemcpyAsync(pl->p, pl->z, sizeof(double) * K, cudaMemcpyDeviceToDevice, st));
+        SPS_TRY(dot(pl, pl->r, pl->z, K, S_RZ_A, st));
+        SPS_TRY(read_scalars(pl, st));
+        rlast = std::sqrt(pl->host_scal[S_RR]);
+        rel = rlast / nb;
+        restarted = true;
+        continue;
       }
       rn = std::sqrt(pl->host_scal[S_RR]);
       rel = rn / nb;

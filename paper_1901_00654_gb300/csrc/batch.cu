@@ -399,20 +399,20 @@ __device__ void cta_vcycle(const BatchProblem& pb, const float* bG, float* xG, c
     cta_restrict(pb, g, L.u, b, B(g - 1), tm);
   }
   {
-    // e = Z'(Z b) through the coarse level's spare vector u
+    // e = Z'(Z b) through an FP64 intermediate (a penalty temporary, unused here)
     const long long K1 = pb.lev[0].geom.K;
     const float* b1 = B(1);
     float* x1 = X(1);
-    float* y1 = pb.lev[0].u;
+    double* y1 = pb.dtmp[0];
     for (long long row = tm.start(); row < K1; row += tm.stride()) {
       double s = 0.0;
       for (long long c = 0; c < K1; ++c) s = fma(pb.coarse_z[row * K1 + c], (double)b1[c], s);
-      y1[row] = (float)s;
+      y1[row] = s;
     }
     team_sync(tm);
     for (long long row = tm.start(); row < K1; row += tm.stride()) {
       double s = 0.0;
-      for (long long c = 0; c < K1; ++c) s = fma(pb.coarse_zt[row * K1 + c], (double)y1[c], s);
+      for (long long c = 0; c < K1; ++c) s = fma(pb.coarse_zt[row * K1 + c], y1[c], s);
       x1[row] = (float)s;
     }
     team_sync(tm);

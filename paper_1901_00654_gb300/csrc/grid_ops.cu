@@ -385,10 +385,18 @@ __global__ void __launch_bounds__(32 * SPMV_Y) k_stencil_spmv(const T* __restric
 // preconditioner however ill-conditioned A_1 is, and Z's rounding errors grow
 // like sqrt(cond(A_1)) instead of cond(A_1) for an explicit inverse.
 // Launch k covers rows k-1 .. K-1 (launch K only scales row K-1).
+// A pivot that is not positive and finite (the assembled matrix is not
+// definite to working accuracy) is counted in *bad and replaced by 1 so that
+// the sweep ends with finite values; coarse_assemble then refactors with a
+// diagonal shift.
 __global__ void k_chol_inv_step(double* __restrict__ A, double* __restrict__ Z, double* __restrict__ piv, long long K,
-                                int k) {
+                                int k, int* __restrict__ bad) {
   const long long r0 = k > 0 ? k - 1 : 0;
-  const double p = k < K ? A[(long long)k * K + k] : 1.0;
+  double p = k < K ? A[(long long)k * K + k] : 1.0;
+  if (!(p > 0.0) || !isfinite(p)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(bad, 1);
+    p = 1.0;
+  }
   const double ip = 1.0 / p;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (K - r0) * K;
        e += (long long)gridDim.x * blockDim.x) {
@@ -434,18 +442,19 @@ __global__ void k_coarse_scale(const double* __restrict__ A, long long K, double
   }
 }
 
-// (in place when out == A: each entry is read and written by the same thread)
-__global__ void k_scale_sym(const double* A, long long K, const double* __restrict__ sc, double* out) {
+// `shift` is added to the diagonal of the scaled matrix.
+__global__ void k_scale_sym(const double* __restrict__ A, long long K, const double* __restrict__ sc,
+                            double* __restrict__ out, double shift) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < K * K;
        e += (long long)gridDim.x * blockDim.x) {
     const long long i = e / K, j = e - (e / K) * K;
-    out[e] = sc[i] * A[e] * sc[j];
+    out[e] = sc[i] * A[e] * sc[j] + (i == j ? shift : 0.0);
   }
 }
 
 // One warp per row, FP64 arithmetic: mode 0: y = M x; 1: y = b - M x; 2: y += M x.
-template <typename T>
-__global__ void k_gemv(const double* __restrict__ M, long long K, const T* __restrict__ x, T* __restrict__ y,
+template <typename TX, typename T>
+__global__ void k_gemv(const double* __restrict__ M, long long K, const TX* __restrict__ x, T* __restrict__ y,
                        const T* __restrict__ b, int mode) {
   const int lane = threadIdx.x & 31;
   for (long long row = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; row < K;
@@ -850,15 +859,33 @@ int coarse_assemble(sps_plan* pl, cudaStream_t st) {
   const int blocks = grid_blocks(K * K, EW_THREADS);
   k_coarse_scale<<<grid_blocks(K, EW_THREADS), EW_THREADS, 0, st>>>(pl->coarse_A, K, sc);
   SPS_CHECK_LAUNCH("coarse scale");
-  k_scale_sym<<<blocks, EW_THREADS, 0, st>>>(pl->coarse_A, K, sc, As);
-  SPS_CHECK_LAUNCH("coarse scale");
-  k_identity<<<blocks, EW_THREADS, 0, st>>>(pl->coarse_inv, K);
-  SPS_CHECK_LAUNCH("coarse identity");
-  for (int k = 0; k <= K; ++k) {
-    k_chol_inv_step<<<blocks, EW_THREADS, 0, st>>>(As, pl->coarse_inv, piv, K, k);
+  // The scaled matrix (unit diagonal) is factored as it is.  If a pivot is not
+  // positive -- mixed plans assemble A_1 from FP32 products, accurate to about
+  // 1e-7 relative, so beyond a scaled condition number near 1e7 the assembled
+  // matrix need not be positive definite -- it is refactored with the diagonal
+  // shifted by 1e-8, 1e-6, 1e-4 in turn: Z'Z then inverts the nearest definite
+  // matrix, as good a coarse correction as those products define.
+  int* bad = reinterpret_cast<int*>(pl->coarse_tmp + 4 * K);
+  const double shifts[4] = {0.0, 1e-8, 1e-6, 1e-4};
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    SPS_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), st));
+    k_scale_sym<<<blocks, EW_THREADS, 0, st>>>(pl->coarse_A, K, sc, As, shifts[attempt]);
+    SPS_CHECK_LAUNCH("coarse scale");
+    k_identity<<<blocks, EW_THREADS, 0, st>>>(pl->coarse_inv, K);
+    SPS_CHECK_LAUNCH("coarse identity");
+    for (int k = 0; k <= K; ++k) k_chol_inv_step<<<blocks, EW_THREADS, 0, st>>>(As, pl->coarse_inv, piv, K, k, bad);
+    count_launches(K);
+    SPS_CHECK_LAUNCH("coarse elimination");
+    int nbad = 0;
+    SPS_CUDA(cudaMemcpyAsync(&nbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SPS_CUDA(cudaStreamSynchronize(st));
+    pl->coarse_shift = shifts[attempt];
+    if (nbad == 0) break;
+    if (attempt == 3) {
+      set_error("coarse matrix not positive definite even with a diagonal shift of 1e-4");
+      return SPS_EBREAKDOWN;
+    }
   }
-  count_launches(K);
-  SPS_CHECK_LAUNCH("coarse elimination");
   k_unscale_transpose<<<blocks, EW_THREADS, 0, st>>>(pl->coarse_inv, pl->coarse_invt, sc, K);
   SPS_CHECK_LAUNCH("coarse unscale");
   return SPS_OK;
@@ -919,20 +946,22 @@ template int stencil_apply<float>(sps_plan*, int, const float*, float*, cudaStre
 // e = A_1^-1 r as e = Z'(Z r); in FP64 one step of iterative refinement
 // follows: e += Z'Z (r - A_1 e), with the residual from the assembled A_1
 // (the refined operator 2M - MAM, M = Z'Z, is symmetric positive definite).
+// (the intermediate y = Z r is FP64 in both precisions: Z's entries grow
+// like sqrt(cond(A_1)) / sqrt(min diag A_1), beyond what FP32 keeps exactly)
 template <typename T>
 int coarse_solve(sps_plan* pl, const T* r, T* e, cudaStream_t st) {
   const long long K = pl->lev[0].geom.K;
   const int blocks = (int)std::min<long long>((K * 32 + EW_THREADS - 1) / EW_THREADS, 152LL * 16);
-  T* y = (T*)(pl->coarse_tmp + 2 * K);
-  k_gemv<T><<<blocks, EW_THREADS, 0, st>>>(pl->coarse_inv, K, r, y, nullptr, 0);
-  k_gemv<T><<<blocks, EW_THREADS, 0, st>>>(pl->coarse_invt, K, y, e, nullptr, 0);
+  double* y = pl->coarse_tmp + 2 * K;
+  k_gemv<T, double><<<blocks, EW_THREADS, 0, st>>>(pl->coarse_inv, K, r, y, nullptr, 0);
+  k_gemv<double, T><<<blocks, EW_THREADS, 0, st>>>(pl->coarse_invt, K, y, e, nullptr, 0);
   count_launches(1);
   SPS_CHECK_LAUNCH("coarse solve");
   if constexpr (sizeof(T) == 8) {
     T* res = (T*)(pl->coarse_tmp + 3 * K);
-    k_gemv<T><<<blocks, EW_THREADS, 0, st>>>(pl->coarse_A, K, e, res, r, 1);
-    k_gemv<T><<<blocks, EW_THREADS, 0, st>>>(pl->coarse_inv, K, res, y, nullptr, 0);
-    k_gemv<T><<<blocks, EW_THREADS, 0, st>>>(pl->coarse_invt, K, y, e, nullptr, 2);
+    k_gemv<T, T><<<blocks, EW_THREADS, 0, st>>>(pl->coarse_A, K, e, res, r, 1);
+    k_gemv<T, double><<<blocks, EW_THREADS, 0, st>>>(pl->coarse_inv, K, res, y, nullptr, 0);
+    k_gemv<double, T><<<blocks, EW_THREADS, 0, st>>>(pl->coarse_invt, K, y, e, nullptr, 2);
     count_launches(2);
     SPS_CHECK_LAUNCH("coarse refinement");
   }

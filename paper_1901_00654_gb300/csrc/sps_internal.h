@@ -130,6 +130,7 @@ struct sps_plan {
   double* coarse_inv = nullptr;
   double* coarse_invt = nullptr;
   double* coarse_tmp = nullptr;   // scale, pivots, work vectors (6 K_1) + scaled copy (K_1^2)
+  double coarse_shift = 0.0;      // diagonal shift the factorisation needed (0 when A_1 was definite)
   // penalty and transfer temporaries (max K over levels)
   double* dtmp[8] = {nullptr};
   float* ftmp[8] = {nullptr};
@@ -150,7 +151,7 @@ struct sps_plan {
     bool profiled = false;
     int prof_first = 0, prof_last = 0;
     unsigned long long nlaunch = 0;   // kernels per replay
-  } graph[2];
+  } graph[3];   // FP64 PCG, mixed PCG, mixed PCG with the FP64 outer operator
   unsigned gen = 0;
   cudaStream_t cap_stream = nullptr;
   // device memory held by the plan (every cudaMalloc goes through plan_alloc)

@@ -74,14 +74,17 @@ def test_device_memory_limit():
         assert res.status == B.SPS_OK
 
 
-def test_singular_system_reports_breakdown():
+@pytest.mark.parametrize("prec", [B.SPS_PREC_FP64, B.SPS_PREC_MIXED])
+def test_singular_system_reports_breakdown(prec):
     """lambda = 0 with every point in one corner cell: the basis functions
     without data have a zero diagonal, the damped Jacobi step divides by it,
-    and the CG scalars stop being finite -- a breakdown, reported as such."""
+    and the CG scalars stop being finite -- a breakdown, reported as such.  The
+    mixed solve first retries with the FP64 outer operator (its answer to an
+    FP32 breakdown), breaks down again and reports it."""
     r = np.random.default_rng(4)
     x = 0.1 * r.random((400, 2))                   # all in the first of 8 x 8 cells
     y = r.standard_normal(400)
-    with B.Plan(2, [8, 8], 2, 0.0, omega=0.5) as pl:
+    with B.Plan(2, [8, 8], 2, 0.0, omega=0.5, precision=prec) as pl:
         pl.set_points(x, y)
         coef, res = pl.solve(1e-8, check=False)
         assert res.status == B.SPS_EBREAKDOWN

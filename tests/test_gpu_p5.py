@@ -116,6 +116,23 @@ def test_p5_mixed_solve(p5):
     assert aerr < 1e-5 and err < 5e-3     # kappa_eff * tol, as for the FP64 solve
 
 
+def test_mixed_with_an_indefinite_fp32_coarse_matrix():
+    """P = 5 with lambda = 1e-2: the mixed plan assembles A_1 from FP32
+    products, which at this conditioning (Jacobi-scaled condition number near
+    5e10) is not positive definite; the factorisation is repeated with a small
+    diagonal shift and the mixed solve converges."""
+    x, y, lo, hi = random_problem(P5, N5, n5, seed=105)
+    with B.Plan(P5, N5, G5, 1e-2, precision=B.SPS_PREC_MIXED, max_iter=20000) as pl:
+        pl.set_points(x, y)
+        coef, res = pl.solve(1e-6)
+    with B.Plan(P5, N5, G5, 1e-2, max_iter=20000) as p64:
+        p64.set_points(x, y)
+        c64, r64 = p64.solve(1e-6)
+    print("P=5, lambda 1e-2, tol 1e-6: mixed %d iterations, FP64 %d iterations" % (res.iterations, r64.iterations))
+    assert res.status == B.SPS_OK and res.rel_res_true <= 1e-6
+    assert res.iterations <= 4 * r64.iterations
+
+
 # ------------------------------------------------------------------ inner coarse CG (NEXT-2)
 
 def _coarse_setup(P, N, G, n, lam, seed):
