@@ -63,9 +63,8 @@ __device__ __forceinline__ void cubic_basis(T t, T* b) {
 // each, for four times the resident warps of the one-lane layout.
 template <int P, typename T, typename CT, int MODE, int PRE = 0, int RR = 0>
 __global__ void __launch_bounds__(POINT_THREADS, PRE == 2 ? 5 : 2)
-k_point(const WorkItem* __restrict__ items, const int* __restrict__ run_begin,
-        const unsigned long long* __restrict__ run_cell, const int* __restrict__ run_order,
-        const CT* __restrict__ xs, long long n,
+k_point(const WorkItem* __restrict__ items, const unsigned* __restrict__ item_span,
+        const unsigned* __restrict__ item_cell, const CT* __restrict__ xs, long long n,
         const double* __restrict__ ys, const T* __restrict__ v, T* __restrict__ u, LevelGeom geom,
         int* __restrict__ err, const double* __restrict__ pre = nullptr) {
   constexpr int R = RR > 0 ? RR : (P < 3 ? P : 3);   // dimensions held in a lane's registers
@@ -81,11 +80,11 @@ k_point(const WorkItem* __restrict__ items, const int* __restrict__ run_begin,
   CT* xsh = reinterpret_cast<CT*>(smem_raw + xoff);
 
   const WorkItem it = items[blockIdx.x];
-  const int pbeg = run_begin[it.run_lo];
-  const int npts = run_begin[it.run_hi] - pbeg;
-  // The item's run table (in processing order) is staged in shared memory with
-  // the coordinates, so the run loop reads no global memory before its points.
-  // Items hold at most MAXR runs by construction (the item builder's cap).
+  const int pbeg = it.pbeg;
+  const int npts = it.npts;
+  // The item's run table (in processing order, built at set-up) is staged in
+  // shared memory with the coordinates, so the run loop reads no global memory
+  // before its points.  Items hold at most MAXR runs (the item builder's cap).
   constexpr int MAXR = 128;
   constexpr int CB = 32 / P;                        // bits per dimension of a packed cell offset
   constexpr unsigned CMASK = CB >= 32 ? 0xffffffffu : (1u << CB) - 1u;
@@ -93,13 +92,8 @@ k_point(const WorkItem* __restrict__ items, const int* __restrict__ run_begin,
   __shared__ unsigned int s_cell[MAXR];             // cell - tile origin, CB bits per dimension
   const int nr = min(it.run_hi - it.run_lo, MAXR);
   for (int e = threadIdx.x; e < nr; e += blockDim.x) {
-    const int r = run_order[it.run_lo + e];
-    const unsigned long long pc = run_cell[r];
-    unsigned cl = 0;
-#pragma unroll
-    for (int p = 0; p < P; ++p) cl |= (unsigned)((int)((pc >> (12 * p)) & 0xFFFull) - it.c0[p]) << (CB * p);
-    s_span[e] = (unsigned)(run_begin[r] - pbeg) | ((unsigned)(run_begin[r + 1] - pbeg) << 16);
-    s_cell[e] = cl;
+    s_span[e] = item_span[it.run_lo + e];
+    s_cell[e] = item_cell[it.run_lo + e];
   }
   if (!PRE) {
     // The host sizes the shared memory by the largest item.  Never stage past
@@ -220,84 +214,6 @@ k_point(const WorkItem* __restrict__ items, const int* __restrict__ run_begin,
 #pragma unroll
     for (int k = 0; k < NR; ++k) accr[k] = T(0);
 
-    if constexpr (VREG && MODE == PT_APPLY && R == 2 && !PRE) {
-      // FP32 apply with 16 sums per lane, two points per step: the two points'
-      // basis values, gathers and group reductions are independent chains that
-      // the scheduler interleaves (one point at a time is latency bound).
-      auto basis = [&](int i, T (&bv)[P][4], T& fixw) {
-        fixw = T(1);
-        if (SHARED_BASIS) {
-          const T t = fma(T(xsh[sdim * npts + (i - pbeg)]), sinv, -stsh);
-          const T val = fma(fma(fma(sc3, t, sc2), t, sc1), t, sc0);
-          fixw = __shfl_sync(gmask, val, mfix[0], TPP) * __shfl_sync(gmask, val, 4 + mfix[F > 1 ? 1 : 0], TPP);
-#pragma unroll
-          for (int m = 0; m < 4; ++m) {
-            bv[P - 2][m] = __shfl_sync(gmask, val, 8 + m, TPP);
-            bv[P - 1][m] = __shfl_sync(gmask, val, 12 + m, TPP);
-          }
-        } else {
-#pragma unroll
-          for (int p = 0; p < P; ++p) {
-            const T t = fma(T(xsh[p * npts + (i - pbeg)]), inv[p], -tsh[p]);
-            if (ONEPIECE && p < F) {
-              const int q = ONEPIECE ? p : 0;
-              fixw *= fma(fma(fma(pc3[q], t, pc2[q]), t, pc1[q]), t, pc0[q]);
-            } else if (p >= P - 2) {
-              cubic_basis(t, bv[p]);
-            } else {
-              T b4[4];
-              cubic_basis(t, b4);
-              const int m = mfix[p < F ? p : 0];
-              fixw *= m == 0 ? b4[0] : m == 1 ? b4[1] : m == 2 ? b4[2] : b4[3];
-            }
-          }
-        }
-      };
-      auto gather = [&](const T (&bv)[P][4]) -> T {
-        T g = T(0);
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          T s1 = T(0);
-#pragma unroll
-          for (int d = 0; d < 4; ++d) s1 = fma(bv[P - 1][d], vr[VREG ? a * 4 + d : 0], s1);
-          g = fma(bv[P - 2][a], s1, g);
-        }
-        return g;
-      };
-      int i = i0;
-      for (; i + 1 < i1; i += 2) {
-        T bA[P][4], bB[P][4], fA, fB;
-        basis(i, bA, fA);
-        basis(i + 1, bB, fB);
-        T gA = gather(bA) * fA, gB = gather(bB) * fB;
-#pragma unroll
-        for (int o = TPP / 2; o >= 1; o >>= 1) {
-          gA += __shfl_xor_sync(gmask, gA, o, TPP);
-          gB += __shfl_xor_sync(gmask, gB, o, TPP);
-        }
-        const T wA = gA * fA, wB = gB * fB;
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          const T tA = wA * bA[P - 2][a], tB = wB * bB[P - 2][a];
-#pragma unroll
-          for (int d = 0; d < 4; ++d) accr[a * 4 + d] = fma(tB, bB[P - 1][d], fma(tA, bA[P - 1][d], accr[a * 4 + d]));
-        }
-      }
-      if (i < i1) {
-        T bA[P][4], fA;
-        basis(i, bA, fA);
-        T gA = gather(bA) * fA;
-#pragma unroll
-        for (int o = TPP / 2; o >= 1; o >>= 1) gA += __shfl_xor_sync(gmask, gA, o, TPP);
-        const T wA = gA * fA;
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          const T tA = wA * bA[P - 2][a];
-#pragma unroll
-          for (int d = 0; d < 4; ++d) accr[a * 4 + d] = fma(tA, bA[P - 1][d], accr[a * 4 + d]);
-        }
-      }
-    } else
     for (int i = i0; i < i1; ++i) {
       if constexpr (PRE == 2 && P == 3 && R == 2 && MODE == PT_APPLY) {
         // products b2[b] b3[d] precomputed: 16 multiply-adds each way per lane
@@ -562,8 +478,8 @@ int launch_point(sps_plan* pl, const Level& L, const T* v, T* u, cudaStream_t st
       if constexpr (P == 3) {
         if (L.lanes_r == 2 && L.pre2) {   // products of the last two dimensions precomputed
           static std::atomic<unsigned long long> a22{0};
-          rc = launch_k(k_point<P, T, CT, MODE, 2, 2>, a22, L.nitems, smem_pre, st, L.items, L.run_begin, L.run_cell,
-                        L.run_order, xs, pl->n, (const double*)pl->y_sorted, v, u, L.geom, pl->err_flag,
+          rc = launch_k(k_point<P, T, CT, MODE, 2, 2>, a22, L.nitems, smem_pre, st, L.items, L.item_span, L.item_cell,
+                        xs, pl->n, (const double*)pl->y_sorted, v, u, L.geom, pl->err_flag,
                         (const double*)L.pre2);
           done = true;
         }
@@ -571,16 +487,16 @@ int launch_point(sps_plan* pl, const Level& L, const T* v, T* u, cudaStream_t st
       if constexpr (P == 3 || P == 4) {
         if (!done && L.lanes_r == 2) {
           static std::atomic<unsigned long long> a12{0};
-          rc = launch_k(k_point<P, T, CT, MODE, 1, 2>, a12, L.nitems, smem_pre, st, L.items, L.run_begin, L.run_cell,
-                        L.run_order, xs, pl->n, (const double*)pl->y_sorted, v, u, L.geom, pl->err_flag,
+          rc = launch_k(k_point<P, T, CT, MODE, 1, 2>, a12, L.nitems, smem_pre, st, L.items, L.item_span, L.item_cell,
+                        xs, pl->n, (const double*)pl->y_sorted, v, u, L.geom, pl->err_flag,
                         (const double*)L.pre);
           done = true;
         }
       }
       if (!done) {
         static std::atomic<unsigned long long> a1{0};
-        rc = launch_k(k_point<P, T, CT, MODE, 1>, a1, L.nitems, smem_pre, st, L.items, L.run_begin, L.run_cell,
-                      L.run_order, xs, pl->n, (const double*)pl->y_sorted, v, u, L.geom, pl->err_flag,
+        rc = launch_k(k_point<P, T, CT, MODE, 1>, a1, L.nitems, smem_pre, st, L.items, L.item_span, L.item_cell,
+                      xs, pl->n, (const double*)pl->y_sorted, v, u, L.geom, pl->err_flag,
                       (const double*)L.pre);
         done = true;
       }
@@ -595,17 +511,17 @@ int launch_point(sps_plan* pl, const Level& L, const T* v, T* u, cudaStream_t st
     const int rsel = L.lanes_r ? L.lanes_r : (P == 3 ? 2 : 3);
     bool launched = false;
     if constexpr (TWO_LAYOUTS) {
-      if (rsel == 2 || (P == 3 && MODE != PT_APPLY)) {
+      if (!launched && (rsel == 2 || (P == 3 && MODE != PT_APPLY))) {
         static std::atomic<unsigned long long> ar2{0};
-        rc = launch_k(k_point<P, T, CT, MODE, 0, 2>, ar2, L.nitems, smem, st, L.items, L.run_begin, L.run_cell,
-                      L.run_order, xs, pl->n, (const double*)pl->y_sorted, v, u, L.geom, pl->err_flag,
+        rc = launch_k(k_point<P, T, CT, MODE, 0, 2>, ar2, L.nitems, smem, st, L.items, L.item_span, L.item_cell,
+                      xs, pl->n, (const double*)pl->y_sorted, v, u, L.geom, pl->err_flag,
                       (const double*)nullptr);
         launched = true;
       }
     }
     if (!launched) {
       static std::atomic<unsigned long long> a0{0};
-      rc = launch_k(k_point<P, T, CT, MODE>, a0, L.nitems, smem, st, L.items, L.run_begin, L.run_cell, L.run_order,
+      rc = launch_k(k_point<P, T, CT, MODE>, a0, L.nitems, smem, st, L.items, L.item_span, L.item_cell,
                     xs, pl->n, (const double*)pl->y_sorted, v, u, L.geom, pl->err_flag, (const double*)nullptr);
     }
   }

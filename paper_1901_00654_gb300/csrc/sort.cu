@@ -234,7 +234,7 @@ __global__ void k_tile_items(const unsigned int* __restrict__ run_off, long long
 
 __global__ void k_fill_items(const unsigned int* __restrict__ run_off, const unsigned int* __restrict__ ioff,
                              long long ntile, int cells_per_tile_log, int cap, int P, int tbits, int tb,
-                             WorkItem* __restrict__ items) {
+                             const int* __restrict__ run_begin, WorkItem* __restrict__ items) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < ntile;
        t += (long long)gridDim.x * blockDim.x) {
     unsigned int i0 = ioff[t], i1 = ioff[t + 1];
@@ -246,6 +246,8 @@ __global__ void k_fill_items(const unsigned int* __restrict__ run_off, const uns
       WorkItem it;
       it.run_lo = (int)(r0 + (k - i0) * cap);
       it.run_hi = (int)min((unsigned int)(r0 + (k - i0 + 1) * cap), r1);
+      it.pbeg = run_begin[it.run_lo];
+      it.npts = run_begin[it.run_hi] - it.pbeg;
       for (int p = 0; p < MAXP; ++p) it.c0[p] = p < P ? (tc[p] << tb) : 0;
       for (int p = 0; p < (int)(sizeof(it.pad) / sizeof(int)); ++p) it.pad[p] = 0;
       items[k] = it;
@@ -255,9 +257,13 @@ __global__ void k_fill_items(const unsigned int* __restrict__ run_off, const uns
 
 // Order the runs of each work item by length, longest first (bitonic sort of
 // at most 128 runs in shared memory, ties by run index), so that the lanes of
-// a warp walk runs of similar length.
+// a warp walk runs of similar length; write the order and, per run slot, the
+// run's span relative to the item's first point and its cell relative to the
+// tile origin (32/P bits per dimension).
 __global__ void k_sort_item_runs(const WorkItem* __restrict__ items, const int* __restrict__ run_begin,
-                                 int* __restrict__ run_order) {
+                                 const unsigned long long* __restrict__ run_cell, int P,
+                                 int* __restrict__ run_order, unsigned* __restrict__ item_span,
+                                 unsigned* __restrict__ item_cell) {
   __shared__ long long key[128];
   const WorkItem it = items[blockIdx.x];
   const int nr = it.run_hi - it.run_lo;
@@ -285,14 +291,23 @@ __global__ void k_sort_item_runs(const WorkItem* __restrict__ items, const int* 
       }
       __syncthreads();
     }
-  if (t < nr) run_order[it.run_lo + t] = it.run_lo + (int)(key[t] & 0xFFFFF);
+  if (t < nr) {
+    const int r = it.run_lo + (int)(key[t] & 0xFFFFF);
+    run_order[it.run_lo + t] = r;
+    const int cb = 32 / P;
+    const unsigned long long pc = run_cell[r];
+    unsigned cl = 0;
+    for (int p = 0; p < P; ++p) cl |= (unsigned)((int)((pc >> (12 * p)) & 0xFFFull) - it.c0[p]) << (cb * p);
+    item_span[it.run_lo + t] = (unsigned)(run_begin[r] - it.pbeg) | ((unsigned)(run_begin[r + 1] - it.pbeg) << 16);
+    item_cell[it.run_lo + t] = cl;
+  }
 }
 
 // Point count of every work item.
 __global__ void k_item_npts(const WorkItem* __restrict__ items, const int* __restrict__ run_begin, int nitems,
                             unsigned int* __restrict__ npts) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nitems; k += gridDim.x * blockDim.x)
-    npts[k] = (unsigned)(run_begin[items[k].run_hi] - run_begin[items[k].run_lo]);
+    npts[k] = (unsigned)items[k].npts;
 }
 
 __global__ void k_permute_items(const WorkItem* __restrict__ in, const unsigned int* __restrict__ perm, int nitems,
@@ -412,11 +427,15 @@ int build_level_work(sps_plan* pl, int g, cudaStream_t st) {
     pfree(pl, L.run_begin);
     pfree(pl, L.run_cell);
     pfree(pl, L.run_order);
+    pfree(pl, L.item_span);
+    pfree(pl, L.item_cell);
     L.run_cap = 0;
     const unsigned int cap = nruns + nruns / 4 + 16;
     SPS_TRY(palloc(pl, &L.run_begin, (long long)cap + 1));
     SPS_TRY(palloc(pl, &L.run_cell, (long long)cap));
     SPS_TRY(palloc(pl, &L.run_order, (long long)cap));
+    SPS_TRY(palloc(pl, &L.item_span, (long long)cap));
+    SPS_TRY(palloc(pl, &L.item_cell, (long long)cap));
     L.run_cap = (int)cap;
   }
   L.nruns = (int)nruns;
@@ -445,10 +464,11 @@ int build_level_work(sps_plan* pl, int g, cudaStream_t st) {
   }
   L.nitems = (int)nitems;
   k_fill_items<<<grid_blocks(ntile, 256), 256, 0, st>>>(run_off, item_off, ntile, P * tb, cap, P, tbits, tb,
-                                                        L.items);
+                                                        L.run_begin, L.items);
   SPS_CHECK_LAUNCH("fill items");
   if (nitems > 0) {
-    k_sort_item_runs<<<nitems, 128, 0, st>>>(L.items, L.run_begin, L.run_order);
+    k_sort_item_runs<<<nitems, 128, 0, st>>>(L.items, L.run_begin, L.run_cell, P, L.run_order, L.item_span,
+                                             L.item_cell);
     SPS_CHECK_LAUNCH("sort item runs");
   }
   L.max_item_pts = 0;

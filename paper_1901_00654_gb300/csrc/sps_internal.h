@@ -44,11 +44,13 @@ struct LevelGeom {
   int patch;            // prod E
 };
 
-// One CTA of the point operator: runs [run_lo, run_hi) of one tile.
+// One CTA of the point operator: runs [run_lo, run_hi) of one tile, whose
+// points are [pbeg, pbeg + npts) (contiguous after the sort).
 struct WorkItem {
   int run_lo, run_hi;
+  int pbeg, npts;
   int c0[MAXP];         // tile origin in level cells
-  int pad[8 - 2 - MAXP > 0 ? 8 - 2 - MAXP : 1];
+  int pad[3];
 };
 
 template <typename T>
@@ -66,6 +68,11 @@ struct Level {
   int* run_begin = nullptr;
   unsigned long long* run_cell = nullptr;   // 12 bits per dimension
   int* run_order = nullptr;                 // runs of each item sorted by length (longest first)
+  // the same order as a ready table per run slot: first | end << 16 relative to
+  // the item's first point, and the cell relative to the tile origin (32/P bits
+  // per dimension), so the point operator stages an item's runs with one read
+  unsigned* item_span = nullptr;
+  unsigned* item_cell = nullptr;
   int nruns = 0, run_cap = 0;
   WorkItem* items = nullptr;
   int nitems = 0, item_cap = 0;

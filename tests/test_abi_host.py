@@ -43,9 +43,10 @@ def test_struct_layouts_match_header(B):
 #include <stddef.h>
 #include "sps.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(sps_options), offsetof(sps_options, replace_ratio),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(sps_options), offsetof(sps_options, replace_ratio),
          offsetof(sps_options, precondition), offsetof(sps_options, lanes_r), sizeof(sps_result),
-         offsetof(sps_result, solve_ms));
+         offsetof(sps_result, solve_ms), offsetof(sps_options, coarse_iters), offsetof(sps_options, max_device_bytes),
+         sizeof(sps_batch_shape));
   return 0;
 }
 '''
@@ -56,13 +57,16 @@ int main(void) {
         subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
         vals = [int(v) for v in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
     assert vals == [C.sizeof(B.sps_options), B.sps_options.replace_ratio.offset, B.sps_options.precondition.offset,
-                    B.sps_options.lanes_r.offset, C.sizeof(B.sps_result), B.sps_result.solve_ms.offset]
+                    B.sps_options.lanes_r.offset, C.sizeof(B.sps_result), B.sps_result.solve_ms.offset,
+                    B.sps_options.coarse_iters.offset, B.sps_options.max_device_bytes.offset,
+                    C.sizeof(B.sps_batch_shape)]
 
 
 def test_defaults(B):
     o = B.sps_default_options()
     assert (o.precision, o.nu1, o.nu2, o.omega, o.max_iter) == (B.SPS_PREC_FP64, 1, 1, 0.0, 20000)
     assert (o.hybrid, o.graphs, o.precondition, o.autotune, o.lanes_r) == (1, 1, 1, 0, 0)
+    assert (o.coarse_cg, o.coarse_iters, o.max_device_bytes) == (0, 32, 0)
 
 
 @pytest.mark.parametrize("args", [
@@ -99,7 +103,8 @@ def test_null_handles(B):
     assert B.lib().sps_launch_count(None) == B.SPS_EINVAL
 
 
-@pytest.mark.parametrize("field,value", [("autotune", 2), ("lanes_r", 1), ("lanes_r", 4), ("tile", 3)])
+@pytest.mark.parametrize("field,value", [("autotune", 2), ("lanes_r", 1), ("lanes_r", 4), ("tile", 3),
+                                         ("coarse_cg", 3), ("coarse_iters", 0)])
 def test_plan_create_rejects_bad_options(B, field, value):
     o = B.sps_default_options()
     setattr(o, field, value)
