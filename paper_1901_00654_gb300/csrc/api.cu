@@ -206,6 +206,11 @@ int check_device_errors(sps_plan* pl, cudaStream_t st) {
     set_error("internal error: the point operator's staged points exceeded its shared memory (work skipped)");
     return SPS_EINTERNAL;
   }
+  if (flags & ERR_WAIT) {
+    SPS_CUDA(cudaMemsetAsync(pl->err_flag, 0, sizeof(int), st));
+    set_error("internal error: the point operator's asynchronous copies did not complete in time (work skipped)");
+    return SPS_EINTERNAL;
+  }
   return SPS_OK;
 }
 

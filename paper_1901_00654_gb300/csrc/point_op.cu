@@ -37,6 +37,55 @@ namespace {
 
 __host__ __device__ constexpr int ipow4(int e) { return e <= 0 ? 1 : 4 * ipow4(e - 1); }
 
+// ---- asynchronous copies into shared memory (sm_90+ PTX) ----
+// A CTA's prologue issues every copy of its work item at once -- the run table
+// and the coefficient patch with cp.async, the contiguous coordinate ranges
+// with one TMA bulk copy per dimension, completed on an mbarrier -- so that it
+// waits for one memory round trip instead of one per dependent load chain.
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// Copy BYTES (4, 8 or 16) from global to shared memory; zero-fill when !valid
+// (src is then not read).
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* dst, const void* src, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(smem_addr(dst)), "l"(src), "n"(BYTES),
+               "r"(valid ? BYTES : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+// One arrival that also announces `bytes` of bulk copies to come.
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+// TMA bulk copy global -> shared: both addresses 16-byte aligned, bytes a
+// multiple of 16; completes `bytes` on the mbarrier.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+// Wait for phase `parity` of the mbarrier, giving up after about a second of
+// SM clocks (returns false then).
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity) {
+  const long long t0 = clock64();
+  for (;;) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > (1LL << 31)) return false;
+  }
+}
+
 // Values of the q+1 = 4 cubic B-splines that are nonzero on a cell, at local
 // coordinate t in [0, 1]: b[m] belongs to basis function (cell + m).  They are
 // the four polynomial pieces of the uniform cubic B-spline (de Boor 1978).
@@ -91,23 +140,71 @@ k_point(const WorkItem* __restrict__ items, const unsigned* __restrict__ item_sp
   __shared__ unsigned int s_span[MAXR];             // first | end << 16, relative to pbeg
   __shared__ unsigned int s_cell[MAXR];             // cell - tile origin, CB bits per dimension
   const int nr = min(it.run_hi - it.run_lo, MAXR);
-  for (int e = threadIdx.x; e < nr; e += blockDim.x) {
-    s_span[e] = item_span[it.run_lo + e];
-    s_cell[e] = item_cell[it.run_lo + e];
-  }
+  // Coordinates: dimension p of the item's points is the contiguous range
+  // [p n + pbeg, p n + pbeg + npts) of xs.  Its 16-byte-aligned middle is
+  // fetched by one TMA bulk copy, the at most 2 (E16 - 1) elements at its ends
+  // by cp.async; in shared memory the range starts at offset sh_p = (p n +
+  // pbeg) mod E16 of a 16-byte-aligned array of XS elements, so the middle
+  // lands 16-byte aligned too.  xo[p] + i indexes coordinate p of point i.
+  constexpr int E16 = 16 / (int)sizeof(CT);
+  const int XS = (npts + 2 * E16 - 1) / E16 * E16;
+  int xo[P];
+#pragma unroll
+  for (int p = 0; p < P; ++p) xo[p] = 0;
+  __shared__ __align__(8) unsigned long long s_bar;   // completion of the bulk copies
+  __shared__ int s_fail;
   if (!PRE) {
     // The host sizes the shared memory by the largest item.  Never stage past
     // it: if an item ever exceeded it, its contribution is skipped and the
     // error flag makes the calling sps_* return SPS_EINTERNAL.
     unsigned dsm;
     asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dsm));
-    if (xoff + (size_t)P * npts * sizeof(CT) > dsm) {
+    if (xoff + (size_t)P * XS * sizeof(CT) > dsm || (smem_addr(xsh) & 15u) != 0) {
       if (threadIdx.x == 0) atomicOr(err, ERR_SMEM);
       return;
     }
+    const unsigned bar = smem_addr(&s_bar);
 #pragma unroll
-    for (int p = 0; p < P; ++p)
-      for (int e = threadIdx.x; e < npts; e += blockDim.x) xsh[p * npts + e] = xs[(long long)p * n + pbeg + e];
+    for (int p = 0; p < P; ++p) {
+      const long long g0 = (long long)p * n + pbeg, g1 = g0 + npts;
+      const int sh = (int)(g0 % E16);
+      xo[p] = p * XS + sh - pbeg;
+      CT* dst = xsh + p * XS + sh;                       // element g0 goes to dst[0]
+      const long long a0 = (g0 + E16 - 1) / E16 * E16;   // aligned middle [a0, a1)
+      const long long a1 = g1 / E16 * E16;
+      const long long h1 = a0 < g1 ? a0 : g1, t0 = a1 > a0 ? a1 : a0;
+      // ends: lanes 0 .. E16-2 the head [g0, h1), lanes E16-1 .. 2E16-3 the tail [t0, g1)
+      const int k = threadIdx.x;
+      if (k < E16 - 1) {
+        if (g0 + k < h1) cp_async<sizeof(CT)>(dst + k, xs + g0 + k, true);
+      } else if (k < 2 * (E16 - 1)) {
+        const long long e = t0 + (k - (E16 - 1));
+        if (e < g1) cp_async<sizeof(CT)>(dst + (e - g0), xs + e, true);
+      }
+    }
+    if (threadIdx.x == 0) {
+      s_fail = 0;
+      mbar_init(bar, 1);
+      unsigned bytes = 0;
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        const long long g0 = (long long)p * n + pbeg, g1 = g0 + npts;
+        const long long a0 = (g0 + E16 - 1) / E16 * E16, a1 = g1 / E16 * E16;
+        if (a1 > a0) bytes += (unsigned)((a1 - a0) * sizeof(CT));
+      }
+      mbar_arrive_expect_tx(bar, bytes);
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        const long long g0 = (long long)p * n + pbeg, g1 = g0 + npts;
+        const long long a0 = (g0 + E16 - 1) / E16 * E16, a1 = g1 / E16 * E16;
+        if (a1 > a0)
+          bulk_g2s(xsh + p * XS + (int)(g0 % E16) + (int)(a0 - g0), xs + a0, (unsigned)((a1 - a0) * sizeof(CT)), bar);
+      }
+    }
+  }
+  for (int e = threadIdx.x; e < nr; e += blockDim.x) {
+    cp_async<4>(&s_span[e], item_span + it.run_lo + e, true);
+    cp_async<4>(&s_cell[e], item_cell + it.run_lo + e, true);
   }
   for (int e = threadIdx.x; e < geom.patch; e += blockDim.x) {
     acc[e] = T(0);
@@ -126,10 +223,21 @@ k_point(const WorkItem* __restrict__ items, const unsigned* __restrict__ item_sp
         inb = inb && j < geom.J[p];
         gi += (long long)j * geom.stride[p];
       }
-      vp[e] = inb ? v[gi] : T(0);
+      cp_async<sizeof(T)>(&vp[e], inb ? v + gi : v, inb);
     }
   }
+  if (!PRE && threadIdx.x == 0) {
+    // bounded wait: on time-out the item is skipped and reported, after a
+    // second bounded wait so that no copy is still landing when the CTA exits
+    if (!mbar_wait_bounded(smem_addr(&s_bar), 0)) {
+      atomicOr(err, ERR_WAIT);
+      s_fail = 1;
+      mbar_wait_bounded(smem_addr(&s_bar), 0);
+    }
+  }
+  cp_async_wait_all();
   __syncthreads();
+  if (!PRE && s_fail) return;
 
   const int group = threadIdx.x / TPP;
   const int glane = threadIdx.x % TPP;
@@ -165,6 +273,8 @@ k_point(const WorkItem* __restrict__ items, const unsigned* __restrict__ item_sp
   const int spc = glane & 3;
   const T sinv = sdim == 0 ? inv[0] : sdim == 1 ? inv[P > 1 ? 1 : 0] : sdim == 2 ? inv[P > 2 ? 2 : 0]
                                                                                  : inv[P > 3 ? 3 : 0];
+  const int xos = sdim == 0 ? xo[0] : sdim == 1 ? xo[P > 1 ? 1 : 0] : sdim == 2 ? xo[P > 2 ? 2 : 0]
+                                                                              : xo[P > 3 ? 3 : 0];
   const T sc0 = spc == 0 ? T(1.0 / 6.0) : spc == 1 ? T(2.0 / 3.0) : spc == 2 ? T(1.0 / 6.0) : T(0);
   const T sc1 = spc == 0 ? T(-0.5) : spc == 1 ? T(0) : spc == 2 ? T(0.5) : T(0);
   const T sc2 = spc == 0 ? T(0.5) : spc == 1 ? T(-1) : spc == 2 ? T(0.5) : T(0);
@@ -256,7 +366,7 @@ k_point(const WorkItem* __restrict__ items, const unsigned* __restrict__ item_sp
           fixw *= m == 0 ? bv[p][0] : m == 1 ? bv[p][1] : m == 2 ? bv[p][2] : bv[p][3];
         }
       } else if (SHARED_BASIS) {
-        const T t = fma(T(xsh[sdim * npts + (i - pbeg)]), sinv, -stsh);
+        const T t = fma(T(xsh[xos + i]), sinv, -stsh);
         const T val = fma(fma(fma(sc3, t, sc2), t, sc1), t, sc0);
         fixw = __shfl_sync(gmask, val, mfix[0], TPP) * __shfl_sync(gmask, val, 4 + mfix[F > 1 ? 1 : 0], TPP);
 #pragma unroll
@@ -267,7 +377,7 @@ k_point(const WorkItem* __restrict__ items, const unsigned* __restrict__ item_sp
       } else {
 #pragma unroll
         for (int p = 0; p < P; ++p) {
-          const T xp = T(xsh[p * npts + (i - pbeg)]);
+          const T xp = T(xsh[xo[p] + i]);
           const T t = fma(xp, inv[p], -tsh[p]);
           if (ONEPIECE && p < F) {
             const int q = ONEPIECE ? p : 0;
@@ -458,8 +568,10 @@ template <int P, typename T, typename CT, int MODE>
 int launch_point(sps_plan* pl, const Level& L, const T* v, T* u, cudaStream_t st) {
   if (L.nitems == 0) return SPS_OK;
   // patch accumulator (+ patch of v) + staged coordinates of the largest item's points
+  // (each dimension's staged range is shifted by up to 16 bytes and rounded up)
   const size_t pts = (size_t)L.max_item_pts;
-  const size_t smem = (size_t)(MODE == PT_APPLY ? 2 : 1) * L.geom.patch * sizeof(T) + pts * P * sizeof(CT) + 16;
+  const size_t smem = (size_t)(MODE == PT_APPLY ? 2 : 1) * L.geom.patch * sizeof(T) + pts * P * sizeof(CT) +
+                      48 * P + 16;
   if (smem > POINT_SMEM_MAX) {
     set_error("tile too large for the point operator's shared memory");
     return SPS_EINVAL;
@@ -467,6 +579,10 @@ int launch_point(sps_plan* pl, const Level& L, const T* v, T* u, cudaStream_t st
   const bool timed = MODE == PT_APPLY && g_prof.active && g_prof.used < PROFILE_MAX;
   if (timed) SPS_CUDA(record_event(g_prof.ev[2 * g_prof.used], st));
   const CT* xs = sizeof(CT) == 4 ? (const CT*)pl->x32_sorted : (const CT*)pl->x_sorted;
+  if ((reinterpret_cast<uintptr_t>(xs) & 15) != 0) {   // the bulk copies need 16-byte alignment
+    set_error("sorted coordinates not 16-byte aligned");
+    return SPS_EINTERNAL;
+  }
   int rc = SPS_OK;
   bool done = false;
   if constexpr (sizeof(T) == 8 && MODE == PT_APPLY) {
@@ -548,7 +664,7 @@ size_t point_apply_smem(const sps_plan* pl, const LevelGeom& G, bool fp32) {
   const size_t t = fp32 ? 4 : 8;
   const size_t ct = (fp32 || pl->dtype == SPS_F32) ? 4 : 8;
   const size_t pts = (size_t)runs_per_item(pl->P) * RUN_MAX;
-  return 2 * (size_t)G.patch * t + pts * pl->P * ct + 16;   // the FP64 basis-value path needs less
+  return 2 * (size_t)G.patch * t + pts * pl->P * ct + 48 * pl->P + 16;   // the FP64 basis-value path needs less
 }
 
 template <typename T>

@@ -179,6 +179,7 @@ int cuda_fail(cudaError_t e, const char* what);
 // device error flags (plan->err_flag)
 constexpr int ERR_DOMAIN = 1;     // a coordinate outside [lo, hi] or a non-finite coordinate/response
 constexpr int ERR_SMEM = 2;       // the point operator's staged points exceeded its shared memory
+constexpr int ERR_WAIT = 4;       // the point operator's wait for its asynchronous copies ran out of time
 // propagate a non-OK status code
 #define SPS_TRY(x)                   \
   do {                               \
