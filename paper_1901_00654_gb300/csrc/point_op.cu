@@ -23,7 +23,12 @@
 //    sum-factorised over the lane's R dimensions and reduced across the group
 //    with shuffles.  The layout per level is chosen by the autotuner.
 //  * The shared accumulator is flushed to global memory with atomics, since
-//    neighbouring tiles overlap in q layers of coefficients.
+//    neighbouring tiles overlap in q layers of coefficients.  For P >= 3 the
+//    patch is staged and flushed by rows along the last dimension (one
+//    multi-index decode per row).
+//  * On coordinate-based levels the groups of a warp walk their runs in step
+//    (the warp loops to its longest run, finished groups carry weight 0), and
+//    the FP32 16-sum layout does its multiply-adds on packed float pairs.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -121,6 +126,8 @@ k_point(const WorkItem* __restrict__ items, const unsigned* __restrict__ item_sp
   constexpr int F = P - R;                    // leading dimensions fixed per lane
   constexpr int TPP = ipow4(F);               // lanes per run
   constexpr bool VREG = sizeof(T) == 4;       // FP32: cache the cell's v in registers
+  // FP32 apply with 16 sums per lane: packed two-wide multiply-adds
+  constexpr bool FF2 = VREG && R == 2 && PRE == 0 && MODE == PT_APPLY;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* acc = reinterpret_cast<T*>(smem_raw);
   T* vp = acc + geom.patch;
@@ -206,7 +213,46 @@ k_point(const WorkItem* __restrict__ items, const unsigned* __restrict__ item_sp
     cp_async<4>(&s_span[e], item_span + it.run_lo + e, true);
     cp_async<4>(&s_cell[e], item_cell + it.run_lo + e, true);
   }
-  for (int e = threadIdx.x; e < geom.patch; e += blockDim.x) {
+  // ROWS (P >= 3): the patch is staged and flushed by rows along the last
+  // dimension (stride 1 in the coefficient array), so a thread decodes one
+  // row's multi-index for its E_{P-1} elements instead of one per element.
+  constexpr bool ROWS = P >= 3;
+  const int EL = geom.E[P - 1];
+  const int nrows = geom.patch / EL;
+  const int nl = min(EL, geom.J[P - 1] - it.c0[P - 1]);   // in-range elements of a row
+  auto row_start = [&](int r, bool& inb) -> long long {
+    int rem = r;
+    long long gi = it.c0[P - 1];
+    inb = true;
+#pragma unroll
+    for (int p = P - 2; p >= 0; --p) {
+      const int qd = (int)(((float)rem + 0.5f) * geom.invE[p]);   // rem / E, as below
+      const int m = rem - qd * geom.E[p];
+      rem = qd;
+      const int j = it.c0[p] + m;
+      inb = inb && j < geom.J[p];
+      gi += (long long)j * geom.stride[p];
+    }
+    return gi;
+  };
+  if (ROWS) {
+    uint4* a4 = reinterpret_cast<uint4*>(acc);
+    const int n4 = (int)((size_t)geom.patch * sizeof(T) / 16);
+    for (int e = threadIdx.x; e < n4; e += blockDim.x) a4[e] = make_uint4(0u, 0u, 0u, 0u);
+    for (int e = n4 * (int)(16 / sizeof(T)) + threadIdx.x; e < geom.patch; e += blockDim.x) acc[e] = T(0);
+    if (MODE == PT_APPLY) {
+      for (int r = threadIdx.x; r < nrows; r += blockDim.x) {
+        bool inb;
+        const long long gi = row_start(r, inb);
+        T* dst = vp + r * EL;
+        for (int m = 0; m < EL; ++m) {
+          const bool ok = inb && m < nl;
+          cp_async<sizeof(T)>(dst + m, ok ? v + gi + m : v, ok);
+        }
+      }
+    }
+  }
+  for (int e = threadIdx.x; !ROWS && e < geom.patch; e += blockDim.x) {
     acc[e] = T(0);
     if (MODE == PT_APPLY) {
       int rem = e;
@@ -293,9 +339,21 @@ k_point(const WorkItem* __restrict__ items, const unsigned* __restrict__ item_sp
 
   // one run per thread when TPP == 1 (runs_per_item == ngroups): which lanes hold one
   const unsigned has_run_mask = __ballot_sync(0xffffffffu, group < nr);
-  for (int e = group; e < nr; e += ngroups) {
-    const unsigned span = s_span[e], pc = s_cell[e];
+  // UNIFORM (coordinate-based levels): the groups of a warp take consecutive
+  // runs and walk them in step.  The warp loops to its longest run; a group
+  // past the end of its own run, or without a run, repeats its first point
+  // with weight 0.  The point loop then never diverges, and the shuffles
+  // inside it run on the converged warp.
+  constexpr bool UNIFORM = !PRE;
+  if (UNIFORM) gmask = 0xffffffffu;
+  const int wfirst = (threadIdx.x & ~31) / TPP;   // this warp's first group
+  for (int e = group; UNIFORM ? e - group + wfirst < nr : e < nr; e += ngroups) {
+    const bool act = !UNIFORM || e < nr;
+    const int er = act ? e : e - group + wfirst;   // a run of this warp's round (< nr)
+    const unsigned span = s_span[er], pc = s_cell[er];
     const int i0 = pbeg + (int)(span & 0xFFFFu), i1 = pbeg + (int)(span >> 16);
+    const int len = act ? i1 - i0 : 0;
+    const int nsteps = UNIFORM ? (int)__reduce_max_sync(0xffffffffu, (unsigned)len) : len;
     T tsh[P];
     int base = 0;
 #pragma unroll
@@ -324,7 +382,9 @@ k_point(const WorkItem* __restrict__ items, const unsigned* __restrict__ item_sp
 #pragma unroll
     for (int k = 0; k < NR; ++k) accr[k] = T(0);
 
-    for (int i = i0; i < i1; ++i) {
+    for (int k = 0; k < nsteps; ++k) {
+      const bool live = k < len;
+      const int i = live ? i0 + k : i0;
       if constexpr (PRE == 2 && P == 3 && R == 2 && MODE == PT_APPLY) {
         // products b2[b] b3[d] precomputed: 16 multiply-adds each way per lane
         const double* q = pre + (long long)i * PRE2_STRIDE;
@@ -349,7 +409,7 @@ k_point(const WorkItem* __restrict__ items, const unsigned* __restrict__ item_sp
         continue;
       }
       T bv[P][4];
-      T fixw = T(1);
+      T fixw = live ? T(1) : T(0);
       if (PRE) {
         const double2* q = reinterpret_cast<const double2*>(pre + (long long)i * (4 * P));
 #pragma unroll
@@ -368,7 +428,7 @@ k_point(const WorkItem* __restrict__ items, const unsigned* __restrict__ item_sp
       } else if (SHARED_BASIS) {
         const T t = fma(T(xsh[xos + i]), sinv, -stsh);
         const T val = fma(fma(fma(sc3, t, sc2), t, sc1), t, sc0);
-        fixw = __shfl_sync(gmask, val, mfix[0], TPP) * __shfl_sync(gmask, val, 4 + mfix[F > 1 ? 1 : 0], TPP);
+        fixw *= __shfl_sync(gmask, val, mfix[0], TPP) * __shfl_sync(gmask, val, 4 + mfix[F > 1 ? 1 : 0], TPP);
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
           bv[P - 2][m] = __shfl_sync(gmask, val, 8 + m, TPP);
@@ -396,6 +456,43 @@ k_point(const WorkItem* __restrict__ items, const unsigned* __restrict__ item_sp
             }
           }
         }
+      }
+      if constexpr (FF2) {
+        // Packed FP32 pairs (two multiply-adds per instruction): the 16
+        // products z[a][d] = b_{P-2,a} b_{P-1,d} are formed once and used by
+        // the gather and by the scatter.
+        const float2 b3a = make_float2(bv[P - 1][0], bv[P - 1][1]);
+        const float2 b3b = make_float2(bv[P - 1][2], bv[P - 1][3]);
+        float2 z[4][2];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const float2 ba = make_float2(bv[P - 2][a], bv[P - 2][a]);
+          z[a][0] = __fmul2_rn(ba, b3a);
+          z[a][1] = __fmul2_rn(ba, b3b);
+        }
+        float2 ga = __fmul2_rn(z[0][0], make_float2(vr[0], vr[1]));
+        float2 gb = __fmul2_rn(z[0][1], make_float2(vr[2], vr[3]));
+#pragma unroll
+        for (int a = 1; a < 4; ++a) {
+          ga = __ffma2_rn(z[a][0], make_float2(vr[4 * a], vr[4 * a + 1]), ga);
+          gb = __ffma2_rn(z[a][1], make_float2(vr[4 * a + 2], vr[4 * a + 3]), gb);
+        }
+        T g = ((ga.x + ga.y) + (gb.x + gb.y)) * fixw;
+#pragma unroll
+        for (int o = TPP / 2; o >= 1; o >>= 1) g += __shfl_xor_sync(gmask, g, o, TPP);
+        const T w = g * fixw;
+        const float2 w2 = make_float2(w, w);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            float2 c = make_float2(accr[4 * a + 2 * h], accr[4 * a + 2 * h + 1]);
+            c = __ffma2_rn(w2, z[a][h], c);
+            accr[4 * a + 2 * h] = c.x;
+            accr[4 * a + 2 * h + 1] = c.y;
+          }
+        }
+        continue;
       }
       T s;
       if (MODE == PT_APPLY) {
@@ -493,13 +590,26 @@ k_point(const WorkItem* __restrict__ items, const unsigned* __restrict__ item_sp
         flushed = true;
       }
     }
-    if (!flushed) {
+    if (!flushed && act) {
 #pragma unroll
       for (int k = 0; k < NR; ++k) atomicAdd(&acc[vidx(k)], accr[k]);
     }
   }
   __syncthreads();
 
+  if (ROWS) {
+    for (int r = threadIdx.x; r < nrows; r += blockDim.x) {
+      bool inb;
+      const long long gi = row_start(r, inb);
+      if (!inb) continue;
+      const T* src = acc + r * EL;
+      for (int m = 0; m < nl; ++m) {
+        const T a = src[m];
+        if (a != T(0)) atomicAdd(&u[gi + m], a);
+      }
+    }
+    return;
+  }
   for (int e = threadIdx.x; e < geom.patch; e += blockDim.x) {
     const T a = acc[e];
     if (a == T(0)) continue;
@@ -633,6 +743,15 @@ int launch_point(sps_plan* pl, const Level& L, const T* v, T* u, cudaStream_t st
                       xs, pl->n, (const double*)pl->y_sorted, v, u, L.geom, pl->err_flag,
                       (const double*)nullptr);
         launched = true;
+      }
+      if constexpr (P == 4 && MODE == PT_APPLY) {
+        if (!launched && rsel == 3) {   // 4 lanes per run, each evaluating one piece of dimension 1
+          static std::atomic<unsigned long long> ar3{0};
+          rc = launch_k(k_point<P, T, CT, MODE, 0, 3>, ar3, L.nitems, smem, st, L.items, L.item_span,
+                        L.item_cell, xs, pl->n, (const double*)pl->y_sorted, v, u, L.geom, pl->err_flag,
+                        (const double*)nullptr);
+          launched = true;
+        }
       }
     }
     if (!launched) {
