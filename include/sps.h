@@ -82,8 +82,10 @@ typedef struct sps_options {
     int    precision;      /* SPS_PREC_FP64 (default) or SPS_PREC_MIXED */
     int    nu1, nu2;       /* pre/post Jacobi sweeps per level (default 1, 1) */
     double omega;          /* Jacobi damping; <= 0 (default): per level
-                              4 / (3 lambda_max(D_g^-1 A_g)) by power iteration */
-    int    power_iters;    /* power iterations for omega (default 20) */
+                              1.8 / lambda_hat, lambda_hat an upper estimate of
+                              lambda_max(D_g^-1 A_g) by Lanczos (top Ritz value
+                              plus its residual bound) */
+    int    power_iters;    /* Lanczos steps for lambda_hat (default 20, at most 32) */
     int    max_iter;       /* outer iteration cap (default 20000) */
     int    warm_start;     /* 1: coef passed to sps_solve is the initial guess */
     int    tile;           /* tile side in cells, 0 = automatic per P */
@@ -172,7 +174,7 @@ SPS_API int sps_plan_create(sps_plan** out, int P, int q, const int* intervals, 
  * The caller may free x and y once the call returns.  Synchronises `stream`.
  * Errors: SPS_EINVAL, SPS_EEMPTY (n == 0), SPS_EDOM (a coordinate outside the
  * domain, or a coordinate or response not finite), SPS_ENOMEM, SPS_EBREAKDOWN
- * (the power iteration for omega found no positive eigenvalue), SPS_ECUDA,
+ * (the Lanczos estimate for omega found no positive eigenvalue), SPS_ECUDA,
  * SPS_EINTERNAL. */
 SPS_API int sps_set_points(sps_plan* plan, int64_t n, const void* x, const void* y, int dtype, int mem,
                    void* stream);

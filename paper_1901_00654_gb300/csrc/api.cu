@@ -31,7 +31,8 @@ namespace {
 
 // scalar slots in plan->scal
 constexpr int S_RZ_A = 0, S_PV = 2, S_RR = 3, S_W = 4, S_FLAG = 6, S_RZ_B = 8, S_TMP = 10, S_TMP2 = 12;
-constexpr int NSCAL = 32;   // slots 16.. belong to the inner coarse CG (grid_ops.cu)
+constexpr int NSCAL = 96;   // slots 16..31 belong to the inner coarse CG (grid_ops.cu)
+constexpr int LZ_MAX = 32, LZ_A = 32, LZ_B = 64;   // Lanczos coefficients alpha_j, beta_j^2 (estimate_omega)
 
 // ---- exact 1-D Gram matrices of the cubic B-splines --------------------------
 // Piece m of the uniform cubic B-spline on one cell, as monomial coefficients
@@ -117,6 +118,25 @@ __global__ void k_normalize(double* x, const double* y, long long n, const doubl
   const double s = 1.0 / sqrt(scal[slot]);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     x[i] = y[i] * s;
+}
+
+// Lanczos step: w -= alpha_j q + beta_{j-1} qp (beta_{j-1} = sqrt(scal[bslot]), none when bslot < 0)
+__global__ void k_lanczos_orth(double* w, const double* q, const double* qp, long long n, const double* scal,
+                               int aslot, int bslot) {
+  const double a = scal[aslot];
+  const double b = bslot >= 0 ? sqrt(fmax(scal[bslot], 0.0)) : 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    w[i] = w[i] - a * q[i] - b * qp[i];
+}
+
+// qp <- q; q <- w / beta_j (q <- 0 when beta_j vanishes: the Krylov space is invariant)
+__global__ void k_lanczos_next(double* qp, double* q, const double* w, long long n, const double* scal, int bslot) {
+  const double b2 = scal[bslot];
+  const double inv = b2 > 1e-300 ? 1.0 / sqrt(b2) : 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    qp[i] = q[i];
+    q[i] = w[i] * inv;
+  }
 }
 
 __global__ void k_mul(double* out, const double* a, const double* b, long long n) {
@@ -274,44 +294,120 @@ int vcycle_into(sps_plan* pl, const T* bG, T* xG, cudaStream_t st) {
 
 namespace {
 
-// Largest eigenvalue of D_g^-1 A_g by power iteration on D^-1/2 A D^-1/2
-// (FP32 operator, FP64 vectors); omega_g = 4 / (3 lambda_max).
+// Largest eigenvalue of the symmetric tridiagonal matrix with diagonal a and
+// off-diagonal b (b[j] couples j and j + 1), by bisection on the Sturm count,
+// and the last component of its unit eigenvector by inverse iteration.
+void tridiag_top(const std::vector<double>& a, const std::vector<double>& b, double* theta, double* s_last) {
+  const int m = (int)a.size();
+  double lo = a[0], hi = a[0];
+  for (int j = 0; j < m; ++j) {
+    const double r = (j > 0 ? std::fabs(b[j - 1]) : 0.0) + (j + 1 < m ? std::fabs(b[j]) : 0.0);
+    lo = std::min(lo, a[j] - r);
+    hi = std::max(hi, a[j] + r);
+  }
+  const double tiny = 1e-300;
+  auto below = [&](double x) {   // number of eigenvalues < x (LDL' pivots of T - x I)
+    int c = 0;
+    double d = 1.0;
+    for (int j = 0; j < m; ++j) {
+      d = a[j] - x - (j > 0 ? b[j - 1] * b[j - 1] / d : 0.0);
+      if (d == 0.0) d = -tiny;
+      if (d < 0.0) ++c;
+    }
+    return c;
+  };
+  for (int it = 0; it < 200 && hi - lo > 1e-15 * std::max(std::fabs(hi), std::fabs(lo)); ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (below(mid) == m) hi = mid;   // every eigenvalue below mid
+    else lo = mid;
+  }
+  *theta = hi;
+  // inverse iteration: (T - sigma I) x = x_prev with sigma just above theta
+  const double sigma = hi + 1e-10 * std::max(std::fabs(hi), 1e-30);
+  std::vector<double> x(m, 1.0), c(m), d(m);
+  for (int rep = 0; rep < 3; ++rep) {
+    // Thomas algorithm on the tridiagonal system
+    double piv = a[0] - sigma;
+    if (std::fabs(piv) < tiny) piv = -tiny;
+    c[0] = m > 1 ? b[0] / piv : 0.0;
+    d[0] = x[0] / piv;
+    for (int j = 1; j < m; ++j) {
+      piv = a[j] - sigma - b[j - 1] * c[j - 1];
+      if (std::fabs(piv) < tiny) piv = -tiny;
+      c[j] = j + 1 < m ? b[j] / piv : 0.0;
+      d[j] = (x[j] - b[j - 1] * d[j - 1]) / piv;
+    }
+    x[m - 1] = d[m - 1];
+    for (int j = m - 2; j >= 0; --j) x[j] = d[j] - c[j] * x[j + 1];
+    double nrm = 0.0;
+    for (int j = 0; j < m; ++j) nrm += x[j] * x[j];
+    nrm = std::sqrt(nrm);
+    if (!(nrm > 0.0) || !std::isfinite(nrm)) break;
+    for (int j = 0; j < m; ++j) x[j] /= nrm;
+  }
+  *s_last = std::isfinite(x[m - 1]) ? std::fabs(x[m - 1]) : 1.0;
+}
+
+// omega_g lambda_hat: the damping of the Jacobi smoother relative to the
+// estimate of lambda_max(D_g^-1 A_g).  Below 2 the damped Jacobi sweep, and
+// with nu1 = nu2 the V-cycle, stay symmetric positive definite.
+constexpr double OMEGA_LMAX = 1.8;
+
+// Largest eigenvalue of D_g^-1 A_g, i.e. of S = D^-1/2 A D^-1/2, by m
+// Lanczos steps (FP32 operator on matrix-free levels, FP64 vectors and
+// recurrences, no reorthogonalisation: the largest Ritz value converges
+// first).  lambda_hat = theta + beta_m |s_m|, the top Ritz value of the
+// tridiagonal T_m plus its residual bound, so that lambda_hat bounds
+// lambda_max once the top Ritz value has settled on it; omega_g =
+// OMEGA_LMAX / lambda_hat.
 int estimate_omega(sps_plan* pl, int g, cudaStream_t st) {
   Level& L = pl->lev[g - 1];
   const long long K = L.geom.K;
   const int blocks = grid_blocks(K, 256);
-  double* x = L.d.alpha;
-  double* y = L.d.u;
-  double* s = L.d.b;
+  double* q = L.d.alpha;      // q_j
+  double* w = L.d.u;          // S q_j, then the next Lanczos direction
+  double* s = L.d.b;          // D^-1/2
+  double* qp = pl->dtmp[7];   // q_{j-1}
+  const int m = std::min(std::max(pl->opt.power_iters, 1), LZ_MAX);
   k_sqrt_copy<<<blocks, 256, 0, st>>>(s, L.d.dinv, K);
-  k_hash_fill<<<blocks, 256, 0, st>>>(x, K, 0x5EEDull + (unsigned long long)g);
-  SPS_CHECK_LAUNCH("power init");
-  SPS_TRY(dot(pl, x, x, K, S_TMP, st));
-  k_normalize<<<blocks, 256, 0, st>>>(x, x, K, pl->scal, S_TMP);
-  const int iters = std::max(pl->opt.power_iters, 1);
-  for (int it = 0; it < iters; ++it) {
-    k_mul<<<blocks, 256, 0, st>>>(y, s, x, K);
+  k_hash_fill<<<blocks, 256, 0, st>>>(q, K, 0x5EEDull + (unsigned long long)g);
+  SPS_CHECK_LAUNCH("Lanczos init");
+  SPS_TRY(dot(pl, q, q, K, S_TMP, st));
+  k_normalize<<<blocks, 256, 0, st>>>(q, q, K, pl->scal, S_TMP);
+  SPS_CUDA(cudaMemsetAsync(qp, 0, sizeof(double) * K, st));
+  for (int j = 0; j < m; ++j) {
+    k_mul<<<blocks, 256, 0, st>>>(w, s, q, K);
     if (L.st_d) {   // assembled FP64 level: its stencil product is the cheapest apply
-      SPS_TRY(apply_level<double>(pl, g, y, pl->dtmp[6], st));
-      k_mul<<<blocks, 256, 0, st>>>(y, s, pl->dtmp[6], K);
+      SPS_TRY(apply_level<double>(pl, g, w, pl->dtmp[6], st));
+      k_mul<<<blocks, 256, 0, st>>>(w, s, pl->dtmp[6], K);
     } else {
-      SPS_TRY(vec_cast_d2f(L.f.alpha, y, K, st));
+      SPS_TRY(vec_cast_d2f(L.f.alpha, w, K, st));
       SPS_TRY(apply_level<float>(pl, g, L.f.alpha, L.f.u, st));
-      SPS_TRY(vec_cast_f2d(y, L.f.u, K, st));
-      k_mul<<<blocks, 256, 0, st>>>(y, s, y, K);
+      SPS_TRY(vec_cast_f2d(w, L.f.u, K, st));
+      k_mul<<<blocks, 256, 0, st>>>(w, s, w, K);
     }
-    SPS_TRY(dot(pl, x, y, K, S_TMP2, st));       // Rayleigh quotient (|x| = 1)
-    SPS_TRY(dot(pl, y, y, K, S_TMP, st));
-    k_normalize<<<blocks, 256, 0, st>>>(x, y, K, pl->scal, S_TMP);
-    SPS_CHECK_LAUNCH("power step");
+    SPS_TRY(dot(pl, q, w, K, LZ_A + j, st));   // alpha_j = q_j' S q_j
+    k_lanczos_orth<<<blocks, 256, 0, st>>>(w, q, qp, K, pl->scal, LZ_A + j, j > 0 ? LZ_B + j - 1 : -1);
+    SPS_TRY(dot(pl, w, w, K, LZ_B + j, st));   // beta_j^2
+    k_lanczos_next<<<blocks, 256, 0, st>>>(qp, q, w, K, pl->scal, LZ_B + j);
+    SPS_CHECK_LAUNCH("Lanczos step");
   }
   SPS_TRY(read_scalars(pl, st));
-  const double lmax = pl->host_scal[S_TMP2];
-  if (!(lmax > 0.0) || !std::isfinite(lmax)) {
-    set_error("power iteration for the Jacobi damping failed");
+  std::vector<double> a(m), b(m);
+  for (int j = 0; j < m; ++j) {
+    a[j] = pl->host_scal[LZ_A + j];
+    b[j] = std::sqrt(std::max(pl->host_scal[LZ_B + j], 0.0));
+  }
+  bool finite = true;
+  for (int j = 0; j < m; ++j) finite = finite && std::isfinite(a[j]) && std::isfinite(b[j]);
+  double theta = 0.0, s_last = 1.0;
+  if (finite) tridiag_top(a, b, &theta, &s_last);
+  const double lmax = theta + b[m - 1] * s_last;
+  if (!finite || !(theta > 0.0) || !std::isfinite(lmax)) {
+    set_error("Lanczos estimate of lambda_max for the Jacobi damping failed");
     return SPS_EBREAKDOWN;
   }
-  L.omega = 4.0 / (3.0 * lmax);
+  L.omega = OMEGA_LMAX / lmax;
   return SPS_OK;
 }
 

@@ -597,7 +597,7 @@ k_point(const WorkItem* __restrict__ items, const unsigned* __restrict__ item_sp
   }
   __syncthreads();
 
-  if (ROWS) {
+  if constexpr (ROWS) {
     for (int r = threadIdx.x; r < nrows; r += blockDim.x) {
       bool inb;
       const long long gi = row_start(r, inb);
@@ -608,24 +608,24 @@ k_point(const WorkItem* __restrict__ items, const unsigned* __restrict__ item_sp
         if (a != T(0)) atomicAdd(&u[gi + m], a);
       }
     }
-    return;
-  }
-  for (int e = threadIdx.x; e < geom.patch; e += blockDim.x) {
-    const T a = acc[e];
-    if (a == T(0)) continue;
-    int rem = e;
-    long long gi = 0;
-    bool inb = true;
+  } else {
+    for (int e = threadIdx.x; e < geom.patch; e += blockDim.x) {
+      const T a = acc[e];
+      if (a == T(0)) continue;
+      int rem = e;
+      long long gi = 0;
+      bool inb = true;
 #pragma unroll
-    for (int p = P - 1; p >= 0; --p) {
-      const int qd = (int)(((float)rem + 0.5f) * geom.invE[p]);
-      const int m = rem - qd * geom.E[p];
-      rem = qd;
-      const int j = it.c0[p] + m;
-      inb = inb && j < geom.J[p];
-      gi += (long long)j * geom.stride[p];
+      for (int p = P - 1; p >= 0; --p) {
+        const int qd = (int)(((float)rem + 0.5f) * geom.invE[p]);
+        const int m = rem - qd * geom.E[p];
+        rem = qd;
+        const int j = it.c0[p] + m;
+        inb = inb && j < geom.J[p];
+        gi += (long long)j * geom.stride[p];
+      }
+      if (inb) atomicAdd(&u[gi], a);
     }
-    if (inb) atomicAdd(&u[gi], a);
   }
 }
 
