@@ -339,6 +339,18 @@ SPS_API int sps_get_omega(const sps_plan* plan, double* omega);
 /* Override omega_g (host array of G values, all > 0). */
 SPS_API int sps_set_omega(sps_plan* plan, const double* omega);
 
+/* Host part of the Jacobi damping estimate (Section 3.2, smoothing iteration;
+ * Algorithm 6's omega is not given in the paper): from m Lanczos coefficients
+ * of D_g^-1/2 A_g D_g^-1/2 -- alpha[j] and beta2[j] = beta_j^2, j < m, host
+ * arrays -- theta, the largest eigenvalue of the tridiagonal T_m (diagonal
+ * alpha, off-diagonal beta_0 .. beta_{m-2}), and lambda_hat = theta +
+ * beta_{m-1} |s_m| (s the unit eigenvector of T_m for theta), the upper
+ * estimate of lambda_max that sps_set_points turns into omega_g = 1.8 /
+ * lambda_hat.  Host-only (no device work).  SPS_EINVAL for null pointers or
+ * m outside 1..32, SPS_EBREAKDOWN for non-finite input or theta <= 0. */
+SPS_API int sps_lanczos_estimate(const double* alpha, const double* beta2, int m, double* theta,
+                                 double* lambda_hat);
+
 /* Kernel timing of the point operator (the dominant kernel): between
  * sps_profile_begin and sps_profile_end every launch of the point operator in
  * its apply mode is bracketed by CUDA events on its stream (at most 8192

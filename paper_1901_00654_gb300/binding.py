@@ -32,7 +32,7 @@ EXPORTED = ["sps_default_options", "sps_plan_create", "sps_set_points", "sps_sol
             "sps_set_omega", "sps_probe_fma_rate", "sps_point_apply", "sps_launch_count",
             "sps_profile_begin", "sps_profile_end", "sps_solve_batch", "sps_set_lambda",
             "sps_penalty_apply_noalloc", "sps_get_tuning", "sps_evaluate", "sps_level_matrix",
-            "sps_plan_device_bytes", "sps_solve_batch_shape", "sps_tune_batch"]
+            "sps_plan_device_bytes", "sps_solve_batch_shape", "sps_tune_batch", "sps_lanczos_estimate"]
 
 
 class sps_options(C.Structure):
@@ -87,6 +87,7 @@ def load(path: str | None = None) -> C.CDLL:
         "sps_get_tuning": (I, [P, I, P, P]),
         "sps_evaluate": (I, [P, P, C.c_int64, P, I, P, I, P]),
         "sps_set_omega": (I, [P, P]),
+        "sps_lanczos_estimate": (I, [P, P, I, C.POINTER(D), C.POINTER(D)]),
         "sps_probe_fma_rate": (I, [I, C.POINTER(D), P]),
         "sps_point_apply": (I, [P, I, I, P, P, I, P]),
         "sps_launch_count": (I, [C.POINTER(C.c_uint64)]),
@@ -376,6 +377,18 @@ def sps_get_tuning(plan, level) -> tuple:
 def sps_set_omega(plan, omega) -> None:
     arr = np.ascontiguousarray(omega, dtype=np.float64)
     _check(lib().sps_set_omega(plan, C.c_void_p(arr.ctypes.data)), "sps_set_omega")
+
+
+def sps_lanczos_estimate(alpha, beta2) -> tuple:
+    """(theta, lambda_hat) from Lanczos coefficients alpha_j, beta_j^2 (host only)."""
+    a = np.ascontiguousarray(alpha, dtype=np.float64)
+    b = np.ascontiguousarray(beta2, dtype=np.float64)
+    if a.shape != b.shape or a.ndim != 1:
+        raise ValueError("alpha and beta2 must be 1-D arrays of one length")
+    th, lh = C.c_double(), C.c_double()
+    _check(lib().sps_lanczos_estimate(C.c_void_p(a.ctypes.data), C.c_void_p(b.ctypes.data), a.size,
+                                      C.byref(th), C.byref(lh)), "sps_lanczos_estimate")
+    return th.value, lh.value
 
 
 def sps_plan_device_bytes(plan) -> int:

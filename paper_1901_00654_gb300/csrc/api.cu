@@ -348,6 +348,25 @@ void tridiag_top(const std::vector<double>& a, const std::vector<double>& b, dou
   *s_last = std::isfinite(x[m - 1]) ? std::fabs(x[m - 1]) : 1.0;
 }
 
+// From m Lanczos coefficients alpha_j and beta_j^2: theta, the top Ritz value
+// (top eigenvalue of the tridiagonal T_m), and lambda_hat = theta +
+// beta_{m-1} |s_m| with s the unit eigenvector of T_m for theta.  False when a
+// coefficient is not finite or theta is not positive.
+bool lanczos_lambda_hat(const double* alpha, const double* beta2, int m, double* theta, double* lambda_hat) {
+  std::vector<double> a(m), b(m);
+  bool finite = true;
+  for (int j = 0; j < m; ++j) {
+    a[j] = alpha[j];
+    b[j] = std::sqrt(std::max(beta2[j], 0.0));
+    finite = finite && std::isfinite(a[j]) && std::isfinite(beta2[j]);
+  }
+  if (!finite) return false;
+  double s_last = 1.0;
+  tridiag_top(a, b, theta, &s_last);
+  *lambda_hat = *theta + b[m - 1] * s_last;
+  return *theta > 0.0 && std::isfinite(*lambda_hat);
+}
+
 // omega_g lambda_hat: the damping of the Jacobi smoother relative to the
 // estimate of lambda_max(D_g^-1 A_g).  Below 2 the damped Jacobi sweep, and
 // with nu1 = nu2 the V-cycle, stay symmetric positive definite.
@@ -393,17 +412,8 @@ int estimate_omega(sps_plan* pl, int g, cudaStream_t st) {
     SPS_CHECK_LAUNCH("Lanczos step");
   }
   SPS_TRY(read_scalars(pl, st));
-  std::vector<double> a(m), b(m);
-  for (int j = 0; j < m; ++j) {
-    a[j] = pl->host_scal[LZ_A + j];
-    b[j] = std::sqrt(std::max(pl->host_scal[LZ_B + j], 0.0));
-  }
-  bool finite = true;
-  for (int j = 0; j < m; ++j) finite = finite && std::isfinite(a[j]) && std::isfinite(b[j]);
-  double theta = 0.0, s_last = 1.0;
-  if (finite) tridiag_top(a, b, &theta, &s_last);
-  const double lmax = theta + b[m - 1] * s_last;
-  if (!finite || !(theta > 0.0) || !std::isfinite(lmax)) {
+  double theta = 0.0, lmax = 0.0;
+  if (!lanczos_lambda_hat(pl->host_scal + LZ_A, pl->host_scal + LZ_B, m, &theta, &lmax)) {
     set_error("Lanczos estimate of lambda_max for the Jacobi damping failed");
     return SPS_EBREAKDOWN;
   }
@@ -1496,6 +1506,18 @@ int sps_level_matrix(sps_plan* pl, int level, double* out, int64_t* entries, int
   SPS_TRY(vec_cast_f2d(od, L.st_f, count, st));
   SPS_CUDA(cudaStreamSynchronize(st));
   return finish_out(out, od, count, mem, st);
+}
+
+int sps_lanczos_estimate(const double* alpha, const double* beta2, int m, double* theta, double* lambda_hat) {
+  if (!alpha || !beta2 || !theta || !lambda_hat || m < 1 || m > LZ_MAX) {
+    set_error("sps_lanczos_estimate: null pointer or m outside 1..32");
+    return SPS_EINVAL;
+  }
+  if (!lanczos_lambda_hat(alpha, beta2, m, theta, lambda_hat)) {
+    set_error("sps_lanczos_estimate: non-finite coefficients or no positive Ritz value");
+    return SPS_EBREAKDOWN;
+  }
+  return SPS_OK;
 }
 
 int sps_get_omega(const sps_plan* pl, double* omega) {

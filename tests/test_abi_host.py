@@ -7,6 +7,7 @@ import re
 import subprocess
 import tempfile
 
+import numpy as np
 import pytest
 
 from paper_1901_00654_gb300 import build
@@ -128,3 +129,57 @@ def test_evaluate_rejects_bad_arguments(B):
         assert B.lib().sps_evaluate(h, None, 0, None, 7, None, 0, None) == B.SPS_EINVAL
     finally:
         B.lib().sps_destroy(h)
+
+
+def _lanczos(S, m, seed):
+    """m steps of the plain Lanczos recurrence on the symmetric matrix S
+    (no reorthogonalisation, as the library runs it): alpha_j and beta_j^2."""
+    rng = np.random.default_rng(seed)
+    q = rng.standard_normal(S.shape[0])
+    q /= np.linalg.norm(q)
+    qp = np.zeros_like(q)
+    a, b2, beta = [], [], 0.0
+    for _ in range(m):
+        w = S @ q
+        alpha = q @ w
+        w = w - alpha * q - beta * qp
+        a.append(alpha)
+        b2.append(w @ w)
+        beta = np.sqrt(b2[-1])
+        qp, q = q, (w / beta if beta > 0 else np.zeros_like(w))
+    return np.array(a), np.array(b2)
+
+
+@pytest.mark.parametrize("n, m", [(12, 12), (300, 20), (300, 32), (5, 1)])
+def test_lanczos_estimate_of_the_damping(B, n, m):
+    """Host logic of omega_g (no GPU): the top Ritz value equals the largest
+    eigenvalue of the Lanczos tridiagonal T_m (numpy), the estimate adds the
+    Ritz residual beta_m |s_m| so that it bounds lambda_max(S) once the Ritz
+    value has converged, and with m = n (an invariant Krylov space) it is
+    lambda_max itself."""
+    rng = np.random.default_rng(n + m)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    ev = np.concatenate([[2.0], rng.uniform(0.05, 1.7, n - 1)])   # a gap below lambda_max = 2
+    S = (Q * ev) @ Q.T
+    a, b2 = _lanczos(S, m, seed=n)
+    theta, lhat = B.sps_lanczos_estimate(a, b2)
+    b = np.sqrt(b2)
+    T = np.diag(a) + np.diag(b[:m - 1], 1) + np.diag(b[:m - 1], -1)
+    w, V = np.linalg.eigh(T)
+    assert abs(theta - w[-1]) <= 1e-12 * abs(w[-1])
+    assert abs(lhat - (w[-1] + b[m - 1] * abs(V[-1, -1]))) <= 1e-9 * w[-1]
+    if m == n:
+        assert abs(theta - 2.0) < 1e-9 and abs(lhat - 2.0) < 1e-6
+    if m >= 20:
+        assert 2.0 <= lhat * (1 + 1e-12) and lhat < 2.0 * 1.05
+
+
+def test_lanczos_estimate_rejects_bad_input(B):
+    with pytest.raises(B.SpsError):
+        B.sps_lanczos_estimate(np.zeros(0), np.zeros(0))
+    with pytest.raises(B.SpsError):
+        B.sps_lanczos_estimate(np.ones(33), np.ones(33))
+    with pytest.raises(B.SpsError):
+        B.sps_lanczos_estimate(np.array([np.nan]), np.array([1.0]))
+    with pytest.raises(B.SpsError):
+        B.sps_lanczos_estimate(np.array([-1.0]), np.array([0.0]))
