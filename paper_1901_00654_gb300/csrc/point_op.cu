@@ -13,8 +13,10 @@
 //    tile of ts^P cells; the (ts+q)^P coefficients its points can touch are
 //    staged in shared memory.
 //  * The item's point coordinates and run table are contiguous after the
-//    sort and are staged in shared memory with coalesced loads before the run
-//    loop (FP64 levels read precomputed basis values instead of coordinates).
+//    sort and are staged in shared memory before the run loop, all copies in
+//    flight at once: TMA bulk copies for the coordinates, cp.async for the
+//    run table and the coefficient patch (FP64 levels read precomputed basis
+//    values instead of coordinates).
 //  * A group of TPP = 4^(P-R) lanes takes one run at a time, R = 2 or 3 being
 //    the number of trailing dimensions a lane holds: each lane owns 4^R of the
 //    cell's (q+1)^P coefficients (16 or 64) and keeps their partial sums in
