@@ -247,6 +247,19 @@ SPS_API int sps_solve_batch_shape(sps_plan* const* plans, int count, double* con
 SPS_API int sps_tune_batch(sps_plan* const* plans, int count, double* const* coefs, int mem, double tol,
                            sps_batch_shape* best, void* stream);
 
+/* The model the batch autotuner minimises (host only; the batched solver has
+ * no counterpart in the paper): the makespan in ms of the persistent queues
+ * of sps_solve_batch_shape for measured per-problem times, t1[i] on a single
+ * CTA and tc[i] on a team of `cluster` CTAs (host arrays of n).  `grid` CTAs
+ * form grid / cluster teams, which take the first `big` problems of `order`
+ * (a permutation of 0 .. n-1, costliest first) with times tc; a team that
+ * finds that queue empty splits into single CTAs, which take the remaining
+ * problems in order with times t1.  cluster = 1: single CTAs take every
+ * problem (big is ignored).  cluster in {1, 2, 4, 8}, grid >= cluster,
+ * 0 <= big <= n; SPS_EINVAL otherwise. */
+SPS_API int sps_simulate_batch(const int* order, const double* t1, const double* tc, int n, int cluster, int big,
+                               int grid, double* makespan_ms);
+
 /* Values s(x_j) = sum_k alpha_k phi_k(x_j) of the spline with coefficients
  * `coef` at m query points: Algorithm 4 (transposed Khatri-Rao product) with
  * the query points in place of the data, on the finest grid of the plan

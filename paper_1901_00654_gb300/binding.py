@@ -32,7 +32,8 @@ EXPORTED = ["sps_default_options", "sps_plan_create", "sps_set_points", "sps_sol
             "sps_set_omega", "sps_probe_fma_rate", "sps_point_apply", "sps_launch_count",
             "sps_profile_begin", "sps_profile_end", "sps_solve_batch", "sps_set_lambda",
             "sps_penalty_apply_noalloc", "sps_get_tuning", "sps_evaluate", "sps_level_matrix",
-            "sps_plan_device_bytes", "sps_solve_batch_shape", "sps_tune_batch", "sps_lanczos_estimate"]
+            "sps_plan_device_bytes", "sps_solve_batch_shape", "sps_tune_batch", "sps_lanczos_estimate",
+            "sps_simulate_batch"]
 
 
 class sps_options(C.Structure):
@@ -88,6 +89,7 @@ def load(path: str | None = None) -> C.CDLL:
         "sps_evaluate": (I, [P, P, C.c_int64, P, I, P, I, P]),
         "sps_set_omega": (I, [P, P]),
         "sps_lanczos_estimate": (I, [P, P, I, C.POINTER(D), C.POINTER(D)]),
+        "sps_simulate_batch": (I, [P, P, P, I, I, I, I, C.POINTER(D)]),
         "sps_probe_fma_rate": (I, [I, C.POINTER(D), P]),
         "sps_point_apply": (I, [P, I, I, P, P, I, P]),
         "sps_launch_count": (I, [C.POINTER(C.c_uint64)]),
@@ -389,6 +391,19 @@ def sps_lanczos_estimate(alpha, beta2) -> tuple:
     _check(lib().sps_lanczos_estimate(C.c_void_p(a.ctypes.data), C.c_void_p(b.ctypes.data), a.size,
                                       C.byref(th), C.byref(lh)), "sps_lanczos_estimate")
     return th.value, lh.value
+
+
+def sps_simulate_batch(order, t1, tc, cluster, big, grid) -> float:
+    """Makespan (ms) of the batched solver's queues for per-problem times (host only)."""
+    o = np.ascontiguousarray(order, dtype=np.int32)
+    a = np.ascontiguousarray(t1, dtype=np.float64)
+    b = np.ascontiguousarray(tc, dtype=np.float64)
+    if not (o.ndim == a.ndim == b.ndim == 1 and o.size == a.size == b.size):
+        raise ValueError("order, t1 and tc must be 1-D arrays of one length")
+    out = C.c_double()
+    _check(lib().sps_simulate_batch(C.c_void_p(o.ctypes.data), C.c_void_p(a.ctypes.data), C.c_void_p(b.ctypes.data),
+                                    o.size, cluster, big, grid, C.byref(out)), "sps_simulate_batch")
+    return out.value
 
 
 def sps_plan_device_bytes(plan) -> int:

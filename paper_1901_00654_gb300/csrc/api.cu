@@ -1508,6 +1508,29 @@ int sps_level_matrix(sps_plan* pl, int level, double* out, int64_t* entries, int
   return finish_out(out, od, count, mem, st);
 }
 
+int sps_simulate_batch(const int* order, const double* t1, const double* tc, int n, int cluster, int big, int grid,
+                       double* makespan_ms) {
+  if (!order || !t1 || !tc || !makespan_ms || n < 1 ||
+      (cluster != 1 && cluster != 2 && cluster != 4 && cluster != 8) || grid < cluster || big < 0 || big > n) {
+    set_error("sps_simulate_batch: null pointer or bad sizes");
+    return SPS_EINVAL;
+  }
+  std::vector<char> seen(n, 0);
+  for (int i = 0; i < n; ++i) {
+    if (order[i] < 0 || order[i] >= n || seen[order[i]]) {
+      set_error("sps_simulate_batch: order is not a permutation of 0 .. n-1");
+      return SPS_EINVAL;
+    }
+    seen[order[i]] = 1;
+    if (!(t1[i] >= 0.0) || !(tc[i] >= 0.0) || !std::isfinite(t1[i]) || !std::isfinite(tc[i])) {
+      set_error("sps_simulate_batch: times must be finite and >= 0");
+      return SPS_EINVAL;
+    }
+  }
+  *makespan_ms = batch_makespan(order, t1, tc, n, cluster, cluster == 1 ? 0 : big, grid);
+  return SPS_OK;
+}
+
 int sps_lanczos_estimate(const double* alpha, const double* beta2, int m, double* theta, double* lambda_hat) {
   if (!alpha || !beta2 || !theta || !lambda_hat || m < 1 || m > LZ_MAX) {
     set_error("sps_lanczos_estimate: null pointer or m outside 1..32");

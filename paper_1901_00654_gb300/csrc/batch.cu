@@ -872,6 +872,11 @@ int solve_batch(sps_plan* const* plans, int count, double* const* coefs, int mem
   return worst;
 }
 
+double batch_makespan(const int* order, const double* t1, const double* tc, int n, int C, int big, int grid) {
+  return simulate_batch(std::vector<int>(order, order + n), std::vector<double>(t1, t1 + n),
+                        std::vector<double>(tc, tc + n), C, big, grid);
+}
+
 // The autotuner: solve the batch once per cluster size C in {1, 2, 4, 8} with
 // every problem on a team of C CTAs, keep the measured time of every problem
 // for every C, then choose the cluster size and the number of problems solved

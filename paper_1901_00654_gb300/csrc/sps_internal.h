@@ -283,6 +283,10 @@ int solve_batch(sps_plan* const* plans, int count, double* const* coefs, int mem
                 const sps_batch_shape* shape, sps_result* res, sps_batch_shape* used, cudaStream_t st);
 int tune_batch(sps_plan* const* plans, int count, double* const* coefs, int mem, double tol, sps_batch_shape* best,
                cudaStream_t st);
+// Makespan (ms) of the batched solver's persistent queues for per-problem
+// times t1 (single CTA) and tc (team of C CTAs), problems taken in `order`:
+// the model the batch autotuner minimises (host only).
+double batch_makespan(const int* order, const double* t1, const double* tc, int n, int C, int big, int grid);
 
 // ---- solver (api.cu) ----
 template <typename T>
