@@ -89,12 +89,24 @@ class ServerStats:
 
 
 class Server:
-    """slots: concurrent requests on the GPU; budget_bytes: admission limit."""
+    """slots: concurrent requests on the GPU; budget_bytes: admission limit.
+
+    executor / stream_factory replace the library call and the CUDA streams
+    (both or neither): executor(problem, stream) -> (coef, sps_result, status)
+    runs one request on the given stream.  The default runs it through
+    libsps.so on torch CUDA streams; the replacements let the scheduler be
+    exercised on its own."""
 
     def __init__(self, slots: int = 8, budget_bytes: float = 120e9, precision: int = B.SPS_PREC_MIXED,
-                 tol: float = 1e-8, max_iter: int = 20000, pool_per_shape: int = 2):
-        import torch
-        self.torch = torch
+                 tol: float = 1e-8, max_iter: int = 20000, pool_per_shape: int = 2, executor=None,
+                 stream_factory=None):
+        if (executor is None) != (stream_factory is None):
+            raise ValueError("executor and stream_factory go together")
+        self._executor = executor
+        if stream_factory is None:
+            import torch
+            self.torch = torch
+            stream_factory = torch.cuda.Stream
         self.slots = slots
         self.budget = int(budget_bytes)
         self.precision = precision
@@ -106,7 +118,7 @@ class Server:
         self._cv = threading.Condition(self._lock)
         self._used = 0
         self._in_flight = 0
-        self._free_streams = [torch.cuda.Stream() for _ in range(slots)]
+        self._free_streams = [stream_factory() for _ in range(slots)]
 
     # ---------------------------------------------------------------- plans
     def _get_plan(self, pr):
@@ -136,10 +148,17 @@ class Server:
 
     # ---------------------------------------------------------------- one request
     def _serve(self, idx, req, t0, est, stats):
-        torch = self.torch
         with self._lock:
             stream = self._free_streams.pop()
         t_admit = time.perf_counter() - t0
+        if self._executor is not None:
+            try:
+                coef, res, status = self._executor(req.problem, stream)
+            except Exception:   # a failed request must still release its slot and budget
+                coef, res, status = None, B.sps_result(), B.SPS_EINTERNAL
+            self._finish(idx, req, t_admit, t0, est, stats, stream, coef, res, status)
+            return
+        torch = self.torch
         try:
             with torch.cuda.stream(stream):
                 key, pl = self._get_plan(req.problem)
@@ -154,6 +173,11 @@ class Server:
             status = res.status
         except B.SpsError as e:
             coef, res, status = None, B.sps_result(), e.code
+        except Exception:       # a failed request must still release its slot and budget
+            coef, res, status = None, B.sps_result(), B.SPS_EINTERNAL
+        self._finish(idx, req, t_admit, t0, est, stats, stream, coef, res, status)
+
+    def _finish(self, idx, req, t_admit, t0, est, stats, stream, coef, res, status):
         t_done = time.perf_counter() - t0
         with self._cv:
             stats.completed.append(Completed(idx, req.t_arrival, t_admit, t_done, coef, res, status))
