@@ -172,6 +172,9 @@ SPS_API int sps_plan_create(sps_plan** out, int P, int q, const int* intervals, 
  * right-hand side Phi'y (Algorithm 3), the coarse matrix and its inverse, and
  * omega.  x: n x P row-major, y: n, both of `dtype`, in `mem`.
  * The caller may free x and y once the call returns.  Synchronises `stream`.
+ * Host inputs (mem = SPS_MEM_HOST) pass through a device copy that the call
+ * allocates and frees (cudaFree synchronises the device); callers on a
+ * latency-critical path pass device buffers instead.
  * Errors: SPS_EINVAL, SPS_EEMPTY (n == 0), SPS_EDOM (a coordinate outside the
  * domain, or a coordinate or response not finite), SPS_ENOMEM, SPS_EBREAKDOWN
  * (the Lanczos estimate for omega found no positive eigenvalue), SPS_ECUDA,
