@@ -142,7 +142,8 @@ typedef struct sps_result {
     double solve_ms;       /* wall time of sps_solve (host clock) */
 } sps_result;
 
-/* Fill *opt with the defaults listed above. */
+/* Fill *opt with the defaults listed above (where the paper leaves a parameter
+ * unstated -- nu1, nu2, omega, the stopping rule -- these are this library's readings). */
 SPS_API void sps_default_options(sps_options* opt);
 
 /* Create a plan for P-dimensional cubic (q = 3) tensor-product splines.
@@ -192,16 +193,18 @@ SPS_API int sps_set_points(sps_plan* plan, int64_t n, const void* x, const void*
  * step), SPS_ECUDA, SPS_EINTERNAL. */
 SPS_API int sps_solve(sps_plan* plan, double* coef, int mem, double tol, sps_result* res, void* stream);
 
-/* Change lambda of a plan; takes effect at the next sps_set_points (which
+/* Change lambda, the penalty weight of Section 2.2, of a plan; takes effect at
+ * the next sps_set_points (which
  * recomputes the right-hand side, diagonals, coarse matrix and damping).
  * Lets a pool of plans of one grid shape serve problems with different
  * lambda without new allocations.  Errors: SPS_EINVAL. */
 SPS_API int sps_set_lambda(sps_plan* plan, double lambda);
 
-/* Release the plan and all of its device memory.  NULL is accepted. */
+/* Release the plan and all of its device memory.  NULL is accepted.  (Plan
+ * lifetime: no counterpart in the paper.) */
 SPS_API int sps_destroy(sps_plan* plan);
 
-/* Thread-local message of the last failure (never NULL). */
+/* Thread-local message of the last failure (never NULL; no counterpart in the paper). */
 SPS_API const char* sps_last_error(void);
 
 /* Launch shape of the batched solver (not a step of the paper's method).  The
@@ -232,14 +235,15 @@ typedef struct sps_batch_shape {
 SPS_API int sps_solve_batch(sps_plan* const* plans, int count, double* const* coefs, int mem, double tol,
                             sps_result* results, void* stream);
 
-/* sps_solve_batch with an explicit launch shape (shape may be NULL: as
+/* sps_solve_batch (many problems of Algorithm 8 in one launch; not in the
+ * paper) with an explicit launch shape (shape may be NULL: as
  * sps_solve_batch); *used (may be NULL) receives the shape that ran (a cluster
  * size that cannot be resident on the device falls back to 1). */
 SPS_API int sps_solve_batch_shape(sps_plan* const* plans, int count, double* const* coefs, int mem, double tol,
                                   const sps_batch_shape* shape, sps_result* results, sps_batch_shape* used,
                                   void* stream);
 
-/* Autotuner of the batched solver's shape: solves the batch once for every
+/* Autotuner of the batched solver's shape (not in the paper): solves the batch once for every
  * cluster size 1, 2, 4, 8 with every problem on a team of that size, keeps
  * each problem's measured time per size, and picks the cluster size and the
  * number of problems solved by clusters whose simulated batch time (the two
@@ -294,7 +298,8 @@ SPS_API int sps_plan_device_bytes(const sps_plan* plan, int64_t* bytes);
  * rounded to FP32 and results widened).  They require sps_set_points and
  * synchronise `stream` when an output is in host memory. */
 
-/* K_g, the number of coefficients on level g (1 <= g <= G). */
+/* K_g = prod_p (N_p^(g) + q), the number of coefficients on level g (1 <= g <= G;
+ * Section 3.2 hierarchy, Table 1 for the finest level). */
 SPS_API int sps_coef_count(const sps_plan* plan, int level, int64_t* K);
 
 /* u = (Phi_g'Phi_g + lambda Lambda_g) v on level g, with all n points
@@ -346,13 +351,16 @@ SPS_API int sps_level_matrix(sps_plan* plan, int level, double* out, int64_t* en
 SPS_API int sps_vcycle(sps_plan* plan, int prec, const double* r, double* z, int mem, void* stream);
 
 /* The stable sort of the points: perm[i] = original index of the i-th sorted
- * point and key[i] its Morton key (either pointer may be NULL); n entries. */
+ * point and key[i] its Morton key (either pointer may be NULL); n entries.
+ * The cell of a point follows from the B-spline supports (Section 2.1); the
+ * sort by cell is this library's work decomposition, not the paper's. */
 SPS_API int sps_get_sort(sps_plan* plan, int64_t* perm, uint64_t* key, int mem, void* stream);
 
-/* Jacobi damping omega_g for g = 1..G (omega[g-1]); host memory. */
+/* Jacobi damping omega_g of Algorithm 6 (not given in the paper) for g = 1..G
+ * (omega[g-1]); host memory. */
 SPS_API int sps_get_omega(const sps_plan* plan, double* omega);
 
-/* Override omega_g (host array of G values, all > 0). */
+/* Override omega_g of Algorithm 6 (host array of G values, all > 0). */
 SPS_API int sps_set_omega(sps_plan* plan, const double* omega);
 
 /* Host part of the Jacobi damping estimate (Section 3.2, smoothing iteration;
@@ -367,7 +375,8 @@ SPS_API int sps_set_omega(sps_plan* plan, const double* omega);
 SPS_API int sps_lanczos_estimate(const double* alpha, const double* beta2, int m, double* theta,
                                  double* lambda_hat);
 
-/* Kernel timing of the point operator (the dominant kernel): between
+/* Measurement hook (no counterpart in the paper).  Kernel timing of the point
+ * operator of Algorithms 3 and 4 (the dominant kernel): between
  * sps_profile_begin and sps_profile_end every launch of the point operator in
  * its apply mode is bracketed by CUDA events on its stream (at most 8192
  * launches are timed).  sps_profile_end synchronises those events and returns
@@ -406,10 +415,12 @@ SPS_API int sps_profile_end(double* point_apply_ms, uint64_t* point_apply_launch
 SPS_API int sps_penalty_apply_noalloc(int P, const int* intervals, const double* lo, const double* hi,
                                       double scale, const double* v, double* u, void* stream);
 
-/* Number of CUDA kernels this library has launched in this process so far. */
+/* Number of CUDA kernels this library has launched in this process so far
+ * (measurement hook; no counterpart in the paper). */
 SPS_API int sps_launch_count(uint64_t* count);
 
-/* Timing probe: measured FMA throughput of the device in FMA/s for FP32
+/* Timing probe (no counterpart in the paper; the roofline denominator of the
+ * point operator): measured FMA throughput of the device in FMA/s for FP32
  * (fp=0) or FP64 (fp=1), from a register-resident FMA loop over all SMs. */
 SPS_API int sps_probe_fma_rate(int fp, double* fma_per_s, void* stream);
 
